@@ -1,0 +1,101 @@
+"""Kernel functions k(x, y) of the oracle (plain NumPy, float64).
+
+Test infrastructure: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` leg of ``bench.py`` may import this package.
+
+Kernels (Section 4 of the paper and the synthetic workloads):
+
+* ``gaussian``     exp(-r^2 / l^2)           (Section 4.1, eq. a_gau, with sigma = l^2)
+* ``exponential``  exp(-r / l)               (Section 4.2, eq. a_exp, with sigma = l)
+* ``matern32``     (1 + sqrt3 r/l) exp(-sqrt3 r/l)
+* ``laplace_sl``   1 / (4 pi r)               (Section 4.3, single-layer potential)
+* ``poly``         (1 + x.y)^m                (test kernel: a polynomial of degree m
+                                               in each variable, reproduced exactly by
+                                               Chebyshev interpolation with q > m nodes)
+* ``dmatern32_dl`` d/dl of ``matern32`` = (3 r^2 / l^3) exp(-sqrt3 r/l)
+
+The diagonal of the kernel matrix (i == j) is never taken from these formulas
+for the singular kernel; see ``diag_value``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+KINDS = ("gaussian", "exponential", "matern32", "laplace_sl", "poly", "dmatern32_dl")
+SQRT3 = math.sqrt(3.0)
+
+
+def pairwise_r(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """Euclidean distances |x_i - y_j| by explicit differences (no norm expansion)."""
+    d = X[:, None, :] - Y[None, :, :]
+    return np.sqrt(np.sum(d * d, axis=2))
+
+
+def kmat(kind: str, X: np.ndarray, Y: np.ndarray, length: float = 1.0,
+         degree: int = 2) -> np.ndarray:
+    """Matrix of off-diagonal kernel values k(X_i, Y_j)."""
+    if kind == "poly":
+        return (1.0 + X @ Y.T) ** degree
+    r = pairwise_r(X, Y)
+    if kind == "gaussian":
+        return np.exp(-(r * r) / (length * length))
+    if kind == "exponential":
+        return np.exp(-r / length)
+    if kind == "matern32":
+        u = SQRT3 * r / length
+        return (1.0 + u) * np.exp(-u)
+    if kind == "dmatern32_dl":
+        u = SQRT3 * r / length
+        return (3.0 * r * r / length ** 3) * np.exp(-u)
+    if kind == "laplace_sl":
+        with np.errstate(divide="ignore"):
+            return 1.0 / (4.0 * math.pi * r)
+    raise ValueError(f"unknown kernel {kind!r}")
+
+
+def self_value(kind: str, X: np.ndarray, length: float = 1.0, degree: int = 2) -> np.ndarray:
+    """k(x_i, x_i) for each point (the kernel's value at zero distance)."""
+    n = X.shape[0]
+    if kind in ("gaussian", "exponential", "matern32"):
+        return np.ones(n)
+    if kind == "dmatern32_dl":
+        return np.zeros(n)
+    if kind == "poly":
+        return (1.0 + np.sum(X * X, axis=1)) ** degree
+    if kind == "laplace_sl":
+        return np.full(n, np.inf)   # singular: a diagonal override is required
+    raise ValueError(f"unknown kernel {kind!r}")
+
+
+def diag_value(kind: str, X: np.ndarray, weights, diag, nugget: float, length: float = 1.0,
+               degree: int = 2) -> np.ndarray:
+    """Diagonal entries A_ii of the kernel matrix.
+
+    A_ii = diag_i + nugget when a per-point override is given (the surface kernel
+    of Section 4.3 replaces the singular self-interaction by a geometric value),
+    else w_i k(x_i, x_i) + nugget (eqs. a_gau and a_exp: 1 + c).
+    """
+    if diag is not None:
+        return np.asarray(diag, dtype=np.float64) + nugget
+    w = np.ones(X.shape[0]) if weights is None else np.asarray(weights, dtype=np.float64)
+    return w * self_value(kind, X, length, degree) + nugget
+
+
+def surface_diag(areas: np.ndarray) -> np.ndarray:
+    """Self-interaction of a flat panel of area a for the single-layer kernel with
+    symmetric weights: a * sqrt(a/pi) / 2 (the workload's diagonal)."""
+    a = np.asarray(areas, dtype=np.float64)
+    return a * np.sqrt(a / math.pi) / 2.0
+
+
+def dense_kernel_matrix(kind: str, X: np.ndarray, length: float = 1.0, nugget: float = 0.0,
+                        weights=None, diag=None, degree: int = 2) -> np.ndarray:
+    """The dense N x N matrix A_ij = sqrt(w_i) k(x_i, x_j) sqrt(w_j), A_ii = diag."""
+    K = kmat(kind, X, X, length, degree)
+    if weights is not None:
+        s = np.sqrt(np.asarray(weights, dtype=np.float64))
+        K = s[:, None] * K * s[None, :]
+    np.fill_diagonal(K, diag_value(kind, X, weights, diag, nugget, length, degree))
+    return K
