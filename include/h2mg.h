@@ -1,0 +1,201 @@
+/* h2mg.h -- C ABI of the GB300 H2-MG library (libh2mg.so).
+ *
+ * H2-MG (Sushnikova, Turkiyyah, Chow, Keyes, "H2-MG: A multigrid method for
+ * hierarchical rank structured matrices") solves A x = b for a dense symmetric
+ * positive definite kernel matrix A held in H2 form,
+ *     A = D + U_1 (D_2 + U_2 ( ... (D_l + U_l S_l V_l) ... ) V_2) V_1      (Sec. 3.1, eq. h2)
+ * with a multigrid V-cycle whose coarse spaces are the nested cluster bases
+ * (Sec. 3.3, Algorithm 1). This header declares the three operations of the
+ * paper's problem statement -- build the H2 matrix from points, a kernel, a leaf
+ * size, a rank and an admissibility parameter; apply it; solve with H2-MG to a
+ * relative-residual tolerance -- plus introspection calls used by tests.
+ *
+ * Conventions (all calls):
+ *  - Pointer arguments for points, vectors, weights and diagonals may be host or
+ *    device memory; the library detects which (cudaPointerGetAttributes) and
+ *    stages host data through its own device buffers. Device pointers must be on
+ *    the current device.
+ *  - Vectors are float64, in the user's point order (the library owns the tree
+ *    permutation). Several right-hand sides are column-major with leading
+ *    dimension ld >= n.
+ *  - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream).
+ *    h2mg_build and h2mg_solve synchronise the stream to read sizes/residuals;
+ *    h2mg_apply returns without synchronising when x and y are device pointers.
+ *  - The caller owns every buffer it passes. The handle owns all device memory it
+ *    allocates; h2mg_destroy frees it.
+ *  - No exception crosses the ABI. Every call returns an h2mg_status; on failure
+ *    h2mg_last_error() returns a message for the calling thread.
+ */
+#ifndef H2MG_H
+#define H2MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct h2mg_matrix_s* h2mg_matrix;   /* opaque, library-owned */
+
+typedef enum {
+    H2MG_OK = 0,
+    H2MG_ERR_INVALID_ARG = 1,    /* bad pointer, size, option; nothing was launched   */
+    H2MG_ERR_OOM = 2,            /* device memory exhausted (or above the set budget)  */
+    H2MG_ERR_CUDA = 3,           /* a CUDA runtime call failed                          */
+    H2MG_ERR_NOT_SPD = 4,        /* Cholesky of the coarse operator met a pivot <= 0    */
+    H2MG_ERR_NOT_CONVERGED = 5,  /* max_cycles reached above tol (info is filled)      */
+    H2MG_ERR_NAN = 6,            /* a NaN/Inf appeared in the input or the residual     */
+    H2MG_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up                  */
+    H2MG_ERR_UNSUPPORTED = 8     /* valid request outside what this build implements    */
+} h2mg_status;
+
+/* Kernel functions k(x, y), r = |x - y| (Sec. 4: eqs. a_gau, a_exp; Sec. 4.3). */
+typedef enum {
+    H2MG_K_GAUSSIAN = 0,      /* exp(-r^2 / length^2)     (Sec. 4.1 with sigma = length^2) */
+    H2MG_K_EXPONENTIAL = 1,   /* exp(-r / length)          (Sec. 4.2 with sigma = length)   */
+    H2MG_K_MATERN32 = 2,      /* (1 + sqrt3 r/length) exp(-sqrt3 r/length)                 */
+    H2MG_K_LAPLACE_SL = 3,    /* 1 / (4 pi r)  single-layer potential (Sec. 4.3); needs diag */
+    H2MG_K_POLY = 4,          /* (1 + x.y)^degree  (test kernel: exact in H2 if degree < q)  */
+    H2MG_K_DMATERN32_DL = 5   /* d/dlength of the Matern-3/2 kernel: (3 r^2/l^3) exp(-sqrt3 r/l) */
+} h2mg_kernel_kind;
+
+/* A_ij = sqrt(w_i) k(x_i, x_j) sqrt(w_j) for i != j;
+ * A_ii = (diag ? diag[i] : w_i k(x_i, x_i)) + nugget       (eqs. a_gau/a_exp: 1 + c). */
+typedef struct {
+    int kind;                 /* h2mg_kernel_kind */
+    double length;            /* length scale, > 0 (ignored by POLY and LAPLACE_SL) */
+    double nugget;            /* added to every diagonal entry */
+    int degree;               /* POLY only, 0..16 */
+    const double* weights;    /* optional, n entries, user order, > 0 (host or device) */
+    const double* diag;       /* optional, n entries, user order (host or device) */
+} h2mg_kernel;
+
+/* Block storage format of the primary copy of D, the couplings S and the coarse
+ * near fields P_i. F64 = IEEE double, products on the FP64 pipe. DF64 = each
+ * entry stored as a pair of floats (hi, lo), hi + lo = the double to ~2^-48
+ * relative, products in double-float arithmetic on the FP32 pipes (same bytes). */
+typedef enum { H2MG_STORE_F64 = 0, H2MG_STORE_DF64 = 1 } h2mg_storage;
+
+typedef struct {
+    int leaf_size;      /* max points per leaf cluster, 2..64 */
+    int cheb_q;         /* Chebyshev nodes per dimension; rank k = q^dim <= 64 */
+    double eta;         /* admissibility: far iff dist > 0 and max(diam) <= eta*dist; >= 0 */
+    int storage;        /* h2mg_storage of the primary copy */
+    int with_f32;       /* 1: also keep an FP32 copy of every V-cycle operator (mixed solves) */
+    int coarse_level;   /* coarsest multigrid level l; -1 = natural l = L - t* + 1 */
+} h2mg_build_opts;
+
+typedef enum { H2MG_PREC_F64 = 0, H2MG_PREC_MIXED_F32 = 1 } h2mg_precision;
+typedef enum { H2MG_OUTER_VCYCLE = 0, H2MG_OUTER_FCG = 1 } h2mg_outer;
+
+typedef struct {
+    double tol;                     /* stop when |b - A x| / |b| <= tol */
+    int max_cycles;                 /* cap on V-cycles (outer iterations), >= 0 */
+    int n_f;                        /* CG iterations on the finest level (Remark rem:fine_coarse) */
+    int n_c;                        /* CG iterations on the coarse levels 2..l-1 */
+    int precision;                  /* h2mg_precision of the V-cycle */
+    int explicit_restrict_residual; /* 1: r_{i+1} = U_i^T (r_i - A_i e_i) with an explicit apply;
+                                       0: use CG's recurrence residual (equal in exact arithmetic) */
+    int outer;                      /* h2mg_outer: repeated V-cycles (Sec. 3.3) or flexible CG
+                                       preconditioned by one V-cycle */
+    int use_graph;                  /* 1: capture one V-cycle as a CUDA graph and replay it */
+} h2mg_solve_opts;
+
+typedef struct {
+    int cycles;                /* V-cycles executed */
+    int converged;             /* 1 if relres <= tol */
+    double relres;             /* final |b - A x| / |b| (float64) */
+    double relres_hist[256];   /* relres before each cycle (first 256) */
+    double ms_solve;           /* wall time of the solve on the stream */
+} h2mg_solve_info;
+
+/* Build the H2 matrix of kernel `k` on `n` points of dimension `dim` (1..3),
+ * row-major n x dim float64 (Sec. 3.1). Tree, block partition, Chebyshev bases,
+ * QR orthonormalisation, couplings, coarse near fields P_i (Sec. 3.3, eq. a2_str)
+ * and the Cholesky factor of the coarsest operator are all computed on the GPU.
+ * Errors: INVALID_ARG (n < 1, dim not in 1..3, leaf/q/eta out of range, null
+ * pointers, NaN coordinates), OOM, NOT_SPD (coarse Cholesky failed), CUDA.
+ * On error *out is NULL and nothing is leaked. */
+h2mg_status h2mg_build(const double* points, int64_t n, int dim, const h2mg_kernel* k,
+                       const h2mg_build_opts* o, void* stream, h2mg_matrix* out);
+
+/* y = A x (Sec. 3.1, the H2 matrix-vector product x_i = V_i x_{i-1},
+ * y_{i-1} = D_i x_{i-1} + U_i y_i). nrhs >= 1 columns, leading dimension ld >= n.
+ * x and y must not overlap. Uses the primary storage copy. */
+h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int64_t ld,
+                       void* stream);
+
+/* Solve A x = b with H2-MG (Algorithm 1, repeated V-cycles, Sec. 3.3). On entry
+ * x holds the initial guess x_0 (zeros are the paper's choice), on exit the
+ * solution. nrhs >= 1 columns (each solved independently), leading dimension ld.
+ * info (optional) receives the last column's statistics. Returns NOT_CONVERGED
+ * (with x and info filled) if max_cycles is reached, NAN if b or a residual is not
+ * finite. */
+h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int64_t ld,
+                       const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream);
+
+/* Free every device buffer of the handle. NULL is accepted. */
+h2mg_status h2mg_destroy(h2mg_matrix A);
+
+/* Static description of a status code. */
+const char* h2mg_error_string(h2mg_status s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* h2mg_last_error(void);
+
+/* ---------------------------------------------------------------- introspection
+ * Used by tests to compare the GPU structures with an independent implementation.
+ * `what` selects an integer: */
+typedef enum {
+    H2MG_Q_N = 0, H2MG_Q_DIM = 1, H2MG_Q_L = 2, H2MG_Q_TSTAR = 3, H2MG_Q_LEVELS = 4,
+    H2MG_Q_KD = 5, H2MG_Q_KC = 6, H2MG_Q_RANK = 7, H2MG_Q_NEAR_PAIRS = 8,
+    H2MG_Q_FAR_PAIRS = 9, H2MG_Q_LEVEL_SIZE = 10, H2MG_Q_BYTES_PRIMARY = 11,
+    H2MG_Q_BYTES_F32 = 12, H2MG_Q_APPLY_BYTES = 13, H2MG_Q_DEVICE_BYTES = 14
+} h2mg_query_what;
+
+/* *value = the quantity `what` (arg = tree level for FAR_PAIRS, multigrid level
+ * for LEVEL_SIZE / APPLY_BYTES, 0 otherwise). APPLY_BYTES = algorithmic bytes
+ * (stored blocks read once plus vectors) of one A_i apply in the primary format. */
+h2mg_status h2mg_query(h2mg_matrix A, int what, int arg, int64_t* value);
+
+typedef enum {
+    H2MG_X_PERM = 0,        /* int32[n]: original index of each tree position       */
+    H2MG_X_LEAF_OFFSETS = 1,/* int32[2^L + 1]: tree-order offsets of the leaves       */
+    H2MG_X_NEAR = 2,        /* int32[2 * pairs]: close leaf pairs (t, s), t <= s      */
+    H2MG_X_FAR = 3,         /* int32[2 * pairs]: far pairs (t, s), t < s, of tree level arg */
+    H2MG_X_RANKS = 4,       /* int32[2^arg]: ranks r_j of the clusters of tree level arg */
+    H2MG_X_BOXES = 5        /* double[2^arg * 2 * dim]: (lo, hi) boxes of tree level arg */
+} h2mg_export_what;
+
+/* Copy the structure `what` to host memory `buf` of `cap` bytes; *bytes = size needed. */
+h2mg_status h2mg_export(h2mg_matrix A, int what, int arg, void* buf, int64_t cap,
+                        int64_t* bytes);
+
+/* y = A_i x for multigrid level i (1..l) of the hierarchy (Sec. 3.3): at i = 1 the
+ * H2 matrix itself in user point order (like h2mg_apply); for i >= 2 the Galerkin
+ * operator on the coefficient space of tree level m(i) = L - i + 2, with k_pad =
+ * KC slots per cluster in cluster order (slots beyond a cluster's rank are zero).
+ * precision selects the primary copy (F64) or the FP32 copy (MIXED_F32). Device
+ * or host vectors; one column. For i = l it applies the dense coarse matrix. */
+h2mg_status h2mg_apply_level(h2mg_matrix A, int level, int precision, const double* x,
+                             double* y, void* stream);
+
+/* e = dir_sol(A_l, r) by the Cholesky factor of the coarsest operator
+ * (Sec. 3.3, Algorithm 1 line dir_sol). Vectors as for h2mg_apply_level at i = l. */
+h2mg_status h2mg_coarse_solve(h2mg_matrix A, const double* r, double* e, void* stream);
+
+/* One call of the smoother Iter(A_i, f, x0) = n iterations of CG (Sec. 3.3) on
+ * multigrid level i; x0 = NULL means zero. x receives the iterate and r (optional)
+ * the recurrence residual. Vectors as for h2mg_apply_level. */
+h2mg_status h2mg_smooth(h2mg_matrix A, int level, int precision, const double* f,
+                        const double* x0, int n, double* x, double* r, void* stream);
+
+/* One V-cycle (Algorithm 1) from x0 with r1 = b - A x0 given: x_out = x0 + e_1. */
+h2mg_status h2mg_vcycle(h2mg_matrix A, const double* x0, const double* r1, double* x_out,
+                        const h2mg_solve_opts* o, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2MG_H */

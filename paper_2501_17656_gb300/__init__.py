@@ -1,0 +1,258 @@
+"""GB300 H2-MG: Python binding of the C library ``libh2mg.so`` (include/h2mg.h).
+
+This module only marshals arguments: every step of the build, the matrix-vector
+product and the H2-MG solve runs in the library's CUDA kernels. It fails loudly if
+the library is missing; there is no CPU fallback.
+
+Vectors may be torch tensors (CUDA or CPU), or NumPy arrays; the library reads
+device pointers in place and stages host pointers itself. Work goes to the current
+torch CUDA stream when torch has CUDA, else to the default stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["H2Matrix", "KERNELS", "SolveInfo", "H2MGError", "load_library", "library_path"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libh2mg.so")
+
+KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "laplace_sl": 3, "poly": 4,
+           "dmatern32_dl": 5}
+STORAGE = {"f64": 0, "df64": 1}
+PRECISION = {"f64": 0, "mixed_f32": 1}
+OUTER = {"vcycle": 0, "fcg": 1}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5: "NOT_CONVERGED",
+          6: "NAN", 7: "TIMEOUT", 8: "UNSUPPORTED"}
+
+Q = dict(N=0, DIM=1, L=2, TSTAR=3, LEVELS=4, KD=5, KC=6, RANK=7, NEAR_PAIRS=8, FAR_PAIRS=9,
+         LEVEL_SIZE=10, BYTES_PRIMARY=11, BYTES_F32=12, APPLY_BYTES=13, DEVICE_BYTES=14)
+X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5)
+
+EXPORTED = ["h2mg_build", "h2mg_apply", "h2mg_solve", "h2mg_destroy", "h2mg_error_string",
+            "h2mg_last_error", "h2mg_query", "h2mg_export", "h2mg_apply_level",
+            "h2mg_coarse_solve", "h2mg_smooth", "h2mg_vcycle"]
+
+
+class H2MGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class _Kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("length", ctypes.c_double), ("nugget", ctypes.c_double),
+                ("degree", ctypes.c_int), ("weights", ctypes.c_void_p), ("diag", ctypes.c_void_p)]
+
+
+class _BuildOpts(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("cheb_q", ctypes.c_int), ("eta", ctypes.c_double),
+                ("storage", ctypes.c_int), ("with_f32", ctypes.c_int), ("coarse_level", ctypes.c_int)]
+
+
+class _SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("n_f", ctypes.c_int),
+                ("n_c", ctypes.c_int), ("precision", ctypes.c_int),
+                ("explicit_restrict_residual", ctypes.c_int), ("outer", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("converged", ctypes.c_int), ("relres", ctypes.c_double),
+                ("relres_hist", ctypes.c_double * 256), ("ms_solve", ctypes.c_double)]
+
+    def history(self):
+        return [self.relres_hist[i] for i in range(min(self.cycles + 1, 256))]
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libh2mg.so (optionally building it first). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(library_path):
+        if not build_if_missing:
+            raise RuntimeError(f"{library_path} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        from . import _build
+        _build.build()
+    lib = ctypes.CDLL(library_path)
+    vp, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.h2mg_build.argtypes = [vp, i64, ci, ctypes.POINTER(_Kernel), ctypes.POINTER(_BuildOpts), vp,
+                               ctypes.POINTER(vp)]
+    lib.h2mg_apply.argtypes = [vp, vp, vp, ci, i64, vp]
+    lib.h2mg_solve.argtypes = [vp, vp, vp, ci, i64, ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    lib.h2mg_destroy.argtypes = [vp]
+    lib.h2mg_error_string.argtypes = [ci]
+    lib.h2mg_error_string.restype = ctypes.c_char_p
+    lib.h2mg_last_error.argtypes = []
+    lib.h2mg_last_error.restype = ctypes.c_char_p
+    lib.h2mg_query.argtypes = [vp, ci, ci, ctypes.POINTER(i64)]
+    lib.h2mg_export.argtypes = [vp, ci, ci, vp, i64, ctypes.POINTER(i64)]
+    lib.h2mg_apply_level.argtypes = [vp, ci, ci, vp, vp, vp]
+    lib.h2mg_coarse_solve.argtypes = [vp, vp, vp, vp]
+    lib.h2mg_smooth.argtypes = [vp, ci, ci, vp, vp, ci, vp, vp, vp]
+    lib.h2mg_vcycle.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_SolveOpts), vp]
+    for name in EXPORTED:
+        if name not in ("h2mg_error_string", "h2mg_last_error"):
+            getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = _lib.h2mg_last_error().decode() or _lib.h2mg_error_string(status).decode()
+        raise H2MGError(status, msg)
+
+
+def _stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or NumPy array (float64, contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not (a.flags.c_contiguous or a.flags.f_contiguous):
+            raise TypeError("arrays must be contiguous float64")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _like(x, n):
+    """A new float64 buffer on the same device/kind as x."""
+    if isinstance(x, np.ndarray):
+        return np.zeros(n, dtype=np.float64)
+    import torch
+    return torch.zeros(n, dtype=torch.float64, device=x.device)
+
+
+class H2Matrix:
+    """An H2 matrix built on the GPU from points and a kernel (Sec. 3.1 of the paper),
+    with its H2-MG multigrid hierarchy (Sec. 3.3)."""
+
+    def __init__(self, points, kernel: str = "gaussian", length: float = 1.0, nugget: float = 0.0,
+                 degree: int = 2, weights=None, diag=None, leaf: int = 64, q: int = 4,
+                 eta: float = 1.0, storage: str = "f64", with_f32: bool = False,
+                 coarse_level: int = -1):
+        lib = load_library()
+        self._lib = lib
+        pts = points
+        if isinstance(pts, np.ndarray):
+            pts = np.ascontiguousarray(pts, dtype=np.float64)
+        n, dim = int(pts.shape[0]), int(pts.shape[1]) if len(pts.shape) > 1 else 1
+        self._keep = [pts, weights, diag]
+        k = _Kernel(KERNELS[kernel], float(length), float(nugget), int(degree), _ptr(weights), _ptr(diag))
+        o = _BuildOpts(int(leaf), int(q), float(eta), STORAGE[storage], int(bool(with_f32)), int(coarse_level))
+        h = ctypes.c_void_p()
+        _check(lib.h2mg_build(_ptr(pts), n, dim, ctypes.byref(k), ctypes.byref(o), _stream(), ctypes.byref(h)))
+        self._h = h
+        self.n, self.dim = n, dim
+        self._keep = None
+
+    # ----------------------------------------------------------------- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.h2mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------------- queries
+    def query(self, what: str, arg: int = 0) -> int:
+        v = ctypes.c_int64()
+        _check(self._lib.h2mg_query(self._h, Q[what], int(arg), ctypes.byref(v)))
+        return int(v.value)
+
+    def export(self, what: str, arg: int = 0) -> np.ndarray:
+        nb = ctypes.c_int64()
+        _check(self._lib.h2mg_export(self._h, X[what], int(arg), None, 0, ctypes.byref(nb)))
+        dtype = np.float64 if what == "BOXES" else np.int32
+        buf = np.zeros(max(int(nb.value) // np.dtype(dtype).itemsize, 1), dtype=dtype)
+        _check(self._lib.h2mg_export(self._h, X[what], int(arg), buf.ctypes.data, buf.nbytes, ctypes.byref(nb)))
+        return buf[: int(nb.value) // np.dtype(dtype).itemsize]
+
+    @property
+    def levels(self) -> int:
+        return self.query("LEVELS")
+
+    def level_size(self, i: int) -> int:
+        return self.query("LEVEL_SIZE", i)
+
+    # ----------------------------------------------------------------- products
+    def apply(self, x, y=None):
+        """y = A x (one or several columns; column-major for NumPy 2-D input)."""
+        if y is None:
+            y = x.clone() if not isinstance(x, np.ndarray) else np.empty_like(x)
+        nrhs = 1 if len(x.shape) == 1 else int(x.shape[1])
+        ld = self.n
+        _check(self._lib.h2mg_apply(self._h, _ptr(x), _ptr(y), nrhs, ld, _stream()))
+        return y
+
+    def apply_level(self, i: int, x, precision: str = "f64", y=None):
+        if y is None:
+            y = _like(x, self.level_size(i))
+        _check(self._lib.h2mg_apply_level(self._h, int(i), PRECISION[precision], _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def coarse_solve(self, r, e=None):
+        if e is None:
+            e = _like(r, self.level_size(self.levels))
+        _check(self._lib.h2mg_coarse_solve(self._h, _ptr(r), _ptr(e), _stream()))
+        return e
+
+    def smooth(self, i: int, f, x0=None, n: int = 1, precision: str = "f64"):
+        x = _like(f, self.level_size(i))
+        r = _like(f, self.level_size(i))
+        _check(self._lib.h2mg_smooth(self._h, int(i), PRECISION[precision], _ptr(f), _ptr(x0), int(n),
+                                     _ptr(x), _ptr(r), _stream()))
+        return x, r
+
+    @staticmethod
+    def _opts(tol=1e-10, max_cycles=100, n_f=1, n_c=40, precision="f64", explicit_restrict_residual=False,
+              outer="vcycle", use_graph=False):
+        return _SolveOpts(float(tol), int(max_cycles), int(n_f), int(n_c), PRECISION[precision],
+                          int(bool(explicit_restrict_residual)), OUTER[outer], int(bool(use_graph)))
+
+    def vcycle(self, x0, r1, **kw):
+        x = _like(x0, self.n)
+        o = self._opts(**kw)
+        _check(self._lib.h2mg_vcycle(self._h, _ptr(x0), _ptr(r1), _ptr(x), ctypes.byref(o), _stream()))
+        return x
+
+    def solve(self, b, x=None, raise_on_fail: bool = True, **kw):
+        """Solve A x = b by H2-MG (Algorithm 1 repeated). Returns (x, SolveInfo)."""
+        if x is None:
+            x = _like(b, b.shape if len(b.shape) > 1 else self.n)
+        nrhs = 1 if len(b.shape) == 1 else int(b.shape[1])
+        o = self._opts(**kw)
+        info = SolveInfo()
+        st = self._lib.h2mg_solve(self._h, _ptr(b), _ptr(x), nrhs, self.n, ctypes.byref(o), ctypes.byref(info),
+                                  _stream())
+        if st != 0 and (raise_on_fail or st not in (5,)):
+            _check(st)
+        return x, info

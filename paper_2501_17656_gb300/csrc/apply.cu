@@ -1,0 +1,602 @@
+// apply.cu -- the level-synchronous H2 matrix-vector product of every multigrid level.
+//
+// Sec. 3.1: y = D x + U_1 (S_1 x_1 + U_2 (... (S_{l-1} x_l + U_l S_l x_l) ...)) with
+// x_i = V_i x_{i-1} (upward pass) and y_{i-1} = D_i x_{i-1} + U_i y_i (downward pass).
+// For multigrid level i >= 2 the operator A_i (eq. a2_str) has the same shape on the
+// coefficients of tree level m(i), with P_i in place of D and the identity as the
+// basis of level m(i).
+//
+// GPU layout: one symmetric block-sparse product (k_bsgemv) covers the close blocks
+// or every coupling level at once: one CTA per block row, each warp streams whole
+// K x K blocks (swizzled so that every warp load is one contiguous 512 B segment),
+// and each block is used twice -- y_t += B x_s for its row and, for s != t, the
+// transposed product B^T x_t for its column, written to the entry's scratch row.
+// The downward pass (k_down_final) gathers those scratch rows, adds the row
+// results and the transfer from the parent, and converts the finest level out.
+//
+// Arithmetic per block format: F64 (DFMA), DF (double-float on the FP32 pipes: the
+// error-free products/sums of Dekker and Knuth), F32 (FP32 FMA). Vectors inside the
+// product are in the same format; the multigrid vectors outside are float64.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace h2mg {
+
+// ----------------------------------------------------------------------------- arithmetic
+template <int FMT>
+struct Ar;
+
+template <>
+struct Ar<FMT_F64> {
+  static constexpr int V = 2;
+  using vec_t = double;
+  using mel_t = double;
+  using acc_t = double;
+  using ld_t = double2;
+  __device__ static acc_t zero() { return 0.0; }
+  __device__ static void decode(const ld_t& v, mel_t* m) {
+    m[0] = v.x;
+    m[1] = v.y;
+  }
+  __device__ static void fma(acc_t& a, mel_t m, vec_t x) { a = ::fma(m, x, a); }
+  __device__ static void add(acc_t& a, acc_t b) { a += b; }
+  __device__ static void norm(acc_t&) {}
+  __device__ static acc_t shfl(acc_t a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+  __device__ static vec_t out(acc_t a) { return a; }
+  __device__ static double to_d(vec_t v) { return v; }
+  __device__ static vec_t from_d(double v) { return v; }
+};
+
+template <>
+struct Ar<FMT_DF> {
+  static constexpr int V = 2;
+  using vec_t = float2;
+  using mel_t = float2;
+  using acc_t = float2;
+  using ld_t = float4;
+  __device__ static acc_t zero() { return make_float2(0.f, 0.f); }
+  __device__ static void decode(const ld_t& v, mel_t* m) {
+    m[0] = make_float2(v.x, v.y);
+    m[1] = make_float2(v.z, v.w);
+  }
+  __device__ static void fma(acc_t& a, mel_t m, vec_t x) { df_fma(a.x, a.y, m.x, m.y, x.x, x.y); }
+  __device__ static void add(acc_t& a, acc_t b) { df_add(a.x, a.y, b.x, b.y); }
+  __device__ static void norm(acc_t& a) { df_norm(a.x, a.y); }
+  __device__ static acc_t shfl(acc_t a, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
+  }
+  __device__ static vec_t out(acc_t a) {
+    df_norm(a.x, a.y);
+    return a;
+  }
+  __device__ static double to_d(vec_t v) { return (double)v.x + (double)v.y; }
+  __device__ static vec_t from_d(double v) {
+    df2 d = df_from_double(v);
+    return make_float2(d.hi, d.lo);
+  }
+};
+
+template <>
+struct Ar<FMT_F32> {
+  static constexpr int V = 4;
+  using vec_t = float;
+  using mel_t = float;
+  using acc_t = float;
+  using ld_t = float4;
+  __device__ static acc_t zero() { return 0.f; }
+  __device__ static void decode(const ld_t& v, mel_t* m) {
+    m[0] = v.x;
+    m[1] = v.y;
+    m[2] = v.z;
+    m[3] = v.w;
+  }
+  __device__ static void fma(acc_t& a, mel_t m, vec_t x) { a = fmaf(m, x, a); }
+  __device__ static void add(acc_t& a, acc_t b) { a += b; }
+  __device__ static void norm(acc_t&) {}
+  __device__ static acc_t shfl(acc_t a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+  __device__ static vec_t out(acc_t a) { return a; }
+  __device__ static double to_d(vec_t v) { return (double)v; }
+  __device__ static vec_t from_d(double v) { return __double2float_rn(v); }
+};
+
+// ----------------------------------------------------------------------------- block GEMV
+// One CTA (8 warps) per block row t of a symmetric upper-stored block operator.
+// yrow[t] = sum_e B_e x_col(e);  z[e] = B_e^T x_t for every off-diagonal entry e.
+template <int K, int FMT>
+__global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
+                                                const int* __restrict__ col,
+                                                const void* const* __restrict__ blk,
+                                                const typename Ar<FMT>::vec_t* __restrict__ x,
+                                                typename Ar<FMT>::vec_t* __restrict__ yrow,
+                                                typename Ar<FMT>::vec_t* __restrict__ z) {
+  using A = Ar<FMT>;
+  using vec_t = typename A::vec_t;
+  using mel_t = typename A::mel_t;
+  using acc_t = typename A::acc_t;
+  using ld_t = typename A::ld_t;
+  constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
+  constexpr int CH = T < LPC ? T : LPC;
+  constexpr int V = A::V, P = 8 / V;
+  __shared__ acc_t red[8][K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int row = blockIdx.x;
+  const int rb = 8 * (lane % LPC), cl = lane / LPC;
+  vec_t xt[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) xt[r] = x[(int64_t)row * K + rb + r];
+  acc_t ya[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) ya[r] = A::zero();
+  const int e0 = rowptr[row], e1 = rowptr[row + 1];
+  for (int e = e0 + w; e < e1; e += 8) {
+    const int s = col[e];
+    const ld_t* B = (const ld_t*)blk[e];
+    const vec_t* xs = x + (int64_t)s * K;
+    const bool off = (s != row);
+#pragma unroll 1
+    for (int ch = 0; ch < T / CH; ++ch) {
+      acc_t zc[CH];
+#pragma unroll
+      for (int tt = 0; tt < CH; ++tt) {
+        const int t = ch * CH + tt;
+        mel_t m[8];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          ld_t v = __ldcs(B + (t * P + k) * 32 + lane);
+          A::decode(v, m + k * V);
+        }
+        const vec_t xv = xs[cl + CPP * t];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) A::fma(ya[r], m[r], xv);
+        acc_t zz = A::zero();
+#pragma unroll
+        for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r]);
+        zc[tt] = zz;
+        if ((t & 3) == 3) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) A::norm(ya[r]);
+        }
+      }
+      if (off) {
+        // reduce the CH partial columns over the LPC lanes that share them
+        if (CH == LPC) {
+#pragma unroll
+          for (int h = CH / 2; h >= 1; h >>= 1) {
+            const bool up = (lane & h) != 0;
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+              acc_t send = up ? zc[j] : zc[j + h];
+              acc_t keep = up ? zc[j + h] : zc[j];
+              acc_t recv = A::shfl(send, h);
+              A::add(keep, recv);
+              zc[j] = keep;
+            }
+          }
+          const int tt = lane & (CH - 1);
+          z[(int64_t)e * K + cl + CPP * (ch * CH + tt)] = A::out(zc[0]);
+        } else {
+#pragma unroll
+          for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0], A::shfl(zc[0], h));
+          if ((lane % LPC) == 0) z[(int64_t)e * K + cl + CPP * (ch * CH)] = A::out(zc[0]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) A::norm(ya[r]);
+  }
+  // rows: sum over the lanes that share them, then over the warps
+#pragma unroll
+  for (int h = LPC; h < 32; h <<= 1)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) A::add(ya[r], A::shfl(ya[r], h));
+  if (lane < LPC)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) red[w][rb + r] = ya[r];
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    acc_t s = red[0][i];
+#pragma unroll
+    for (int ww = 1; ww < 8; ++ww) A::add(s, red[ww][i]);
+    yrow[(int64_t)row * K + i] = A::out(s);
+  }
+}
+
+// ----------------------------------------------------------------------------- passes
+// point vector (float64, user order) -> padded tree slots in the product format
+template <int FMT>
+__global__ void k_pts_in(const double* __restrict__ x, const int* __restrict__ slot_of, int64_t n,
+                         typename Ar<FMT>::vec_t* __restrict__ xp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xp[slot_of[i]] = Ar<FMT>::from_d(x[i]);
+}
+
+// coefficient vector (float64, KC per cluster) -> product format
+template <int FMT>
+__global__ void k_coef_in(const double* __restrict__ x, int64_t n, typename Ar<FMT>::vec_t* __restrict__ xc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xc[i] = Ar<FMT>::from_d(x[i]);
+}
+
+// x_hat(leaf j)[b] = sum_i U_j[i, b] x_j[i]   (UT = U^T, KC x KD column-major)
+template <int FMT, class BT>
+__global__ void k_up_leaf(const BT* __restrict__ UT, int KD, int KC,
+                          const typename Ar<FMT>::vec_t* __restrict__ xp,
+                          typename Ar<FMT>::vec_t* __restrict__ xc) {
+  __shared__ double xs[64];
+  int j = blockIdx.x;
+  for (int i = threadIdx.x; i < KD; i += blockDim.x) xs[i] = Ar<FMT>::to_d(xp[(int64_t)j * KD + i]);
+  __syncthreads();
+  const BT* Uj = UT + (int64_t)j * KD * KC;
+  for (int b = threadIdx.x; b < KC; b += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < KD; ++i) acc += (double)Uj[b + i * KC] * xs[i];
+    xc[(int64_t)j * KC + b] = Ar<FMT>::from_d(acc);
+  }
+}
+
+// x_hat(P)[b] = sum_{c in children(P)} sum_a E'_c[a, b] x_hat(c)[a]  (ET = E'^T)
+template <int FMT, class BT>
+__global__ void k_up(const BT* __restrict__ ET, int KC, const typename Ar<FMT>::vec_t* __restrict__ xch,
+                     typename Ar<FMT>::vec_t* __restrict__ xpar) {
+  __shared__ double xs[128];
+  int p = blockIdx.x;
+  for (int i = threadIdx.x; i < 2 * KC; i += blockDim.x) xs[i] = Ar<FMT>::to_d(xch[(int64_t)2 * p * KC + i]);
+  __syncthreads();
+  for (int b = threadIdx.x; b < KC; b += blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < 2; ++c) {
+      const BT* E = ET + (int64_t)(2 * p + c) * KC * KC;
+      for (int a = 0; a < KC; ++a) acc += (double)E[b + a * KC] * xs[c * KC + a];
+    }
+    xpar[(int64_t)p * KC + b] = Ar<FMT>::from_d(acc);
+  }
+}
+
+// y_hat(c)[a] = yrow(c)[a] + sum_{e in gather(c)} z[e][a] + sum_b E'_c[a, b] y_hat(parent)[b]
+// Writes the product format (yc) or, for the output level, float64 (yout).
+template <int FMT, class BT>
+__global__ void k_down_final(int slot_base, int KC, const typename Ar<FMT>::vec_t* __restrict__ yrow,
+                             const int* __restrict__ gptr, const int* __restrict__ gent,
+                             const typename Ar<FMT>::vec_t* __restrict__ z, const BT* __restrict__ E,
+                             const typename Ar<FMT>::vec_t* __restrict__ ypar,
+                             typename Ar<FMT>::vec_t* __restrict__ yc, double* __restrict__ yout) {
+  using A = Ar<FMT>;
+  __shared__ double ps[64];
+  int c = blockIdx.x;
+  int sl = slot_base + c;
+  if (E)
+    for (int i = threadIdx.x; i < KC; i += blockDim.x) ps[i] = A::to_d(ypar[(int64_t)(c >> 1) * KC + i]);
+  __syncthreads();
+  for (int a = threadIdx.x; a < KC; a += blockDim.x) {
+    typename A::acc_t acc = yrow[(int64_t)sl * KC + a];
+    for (int g = gptr[sl]; g < gptr[sl + 1]; ++g) A::add(acc, z[(int64_t)gent[g] * KC + a]);
+    double v = A::to_d(A::out(acc));
+    if (E) {
+      const BT* Ec = E + (int64_t)c * KC * KC;
+      double t = 0.0;
+      for (int b = 0; b < KC; ++b) t += (double)Ec[a + b * KC] * ps[b];
+      v += t;
+    }
+    if (yout)
+      yout[(int64_t)c * KC + a] = v;
+    else
+      yc[(int64_t)sl * KC + a] = A::from_d(v);
+  }
+}
+
+// y(point) = yrowD + gathered transposes + U y_hat(leaf), scattered to user order.
+template <int FMT, class BT>
+__global__ void k_leaf_final(int KD, int KC, const typename Ar<FMT>::vec_t* __restrict__ yrow,
+                             const int* __restrict__ gptr, const int* __restrict__ gent,
+                             const typename Ar<FMT>::vec_t* __restrict__ z, const BT* __restrict__ U,
+                             const typename Ar<FMT>::vec_t* __restrict__ yleaf,
+                             const int* __restrict__ leafoff, const int* __restrict__ perm,
+                             double* __restrict__ y) {
+  using A = Ar<FMT>;
+  __shared__ double ps[64];
+  int j = blockIdx.x;
+  if (U)
+    for (int i = threadIdx.x; i < KC; i += blockDim.x) ps[i] = A::to_d(yleaf[(int64_t)j * KC + i]);
+  __syncthreads();
+  int p0 = leafoff[j], nj = leafoff[j + 1] - p0;
+  for (int i = threadIdx.x; i < nj; i += blockDim.x) {
+    typename A::acc_t acc = yrow[(int64_t)j * KD + i];
+    for (int g = gptr[j]; g < gptr[j + 1]; ++g) A::add(acc, z[(int64_t)gent[g] * KD + i]);
+    double v = A::to_d(A::out(acc));
+    if (U) {
+      const BT* Uj = U + (int64_t)j * KD * KC;
+      double t = 0.0;
+      for (int b = 0; b < KC; ++b) t += (double)Uj[i + b * KD] * ps[b];
+      v += t;
+    }
+    y[perm[p0 + i]] = v;
+  }
+}
+
+__global__ void k_transpose_blocks(const double* __restrict__ in, int R, int C, double* __restrict__ out) {
+  // per block: in R x C column-major -> out C x R column-major
+  int64_t b = blockIdx.x;
+  for (int e = threadIdx.x; e < R * C; e += blockDim.x) {
+    int i = e % R, j = e / R;
+    out[b * R * C + j + (int64_t)i * C] = in[b * R * C + e];
+  }
+}
+__global__ void k_transpose_blocks32(const float* __restrict__ in, int R, int C, float* __restrict__ out) {
+  int64_t b = blockIdx.x;
+  for (int e = threadIdx.x; e < R * C; e += blockDim.x) {
+    int i = e % R, j = e / R;
+    out[b * R * C + j + (int64_t)i * C] = in[b * R * C + e];
+  }
+}
+
+// ----------------------------------------------------------------------------- host
+struct OpHost {
+  std::vector<int> rowptr, col;
+  std::vector<int64_t> blk;     // block index in the pool of the entry
+  std::vector<int> pool;        // 0: D/S pool, 1: P pool
+  std::vector<int> rowof;
+};
+
+static int64_t upper_pos(const HostCSR& C, int t, int s, bool strict) {
+  auto b = C.col.begin() + C.rowptr[t], e = C.col.begin() + C.rowptr[t + 1];
+  auto it = std::lower_bound(b, e, s);
+  if (it == e || *it != s) return -1;
+  auto first = std::lower_bound(b, e, strict ? t + 1 : t);
+  return it - first;
+}
+
+static std::vector<int64_t> ubase(const HostCSR& C, int nrows, bool strict) {
+  std::vector<int64_t> ub(nrows + 1, 0);
+  for (int t = 0; t < nrows; ++t) {
+    int cnt = 0;
+    for (int e = C.rowptr[t]; e < C.rowptr[t + 1]; ++e) cnt += strict ? (C.col[e] > t) : (C.col[e] >= t);
+    ub[t + 1] = ub[t] + cnt;
+  }
+  return ub;
+}
+
+static SymOp upload_op(Matrix& M, const OpHost& H, int K, const void* pool0, const void* pool1,
+                       const void* pool0_32, const void* pool1_32) {
+  SymOp op;
+  op.K = K;
+  op.nrows = (int)H.rowptr.size() - 1;
+  op.nnz = (int)H.col.size();
+  cudaStream_t s = M.stream;
+  auto up = [&](const void* src, size_t bytes) {
+    void* d = M.alloc(std::max<size_t>(bytes, 8));
+    if (bytes) H2_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+    return d;
+  };
+  op.rowptr = (int*)up(H.rowptr.data(), sizeof(int) * H.rowptr.size());
+  op.col = (int*)up(H.col.data(), sizeof(int) * H.col.size());
+  std::vector<const void*> p(op.nnz), p32(op.nnz);
+  size_t b64 = (size_t)K * K * fmt_bytes(M.fmt), b32 = (size_t)K * K * 4;
+  for (int e = 0; e < op.nnz; ++e) {
+    p[e] = (const char*)(H.pool[e] ? pool1 : pool0) + H.blk[e] * b64;
+    const void* q = H.pool[e] ? pool1_32 : pool0_32;
+    p32[e] = q ? (const char*)q + H.blk[e] * b32 : nullptr;
+  }
+  op.blk = (const void**)up(p.data(), sizeof(void*) * p.size());
+  op.blk32 = (const void**)up(p32.data(), sizeof(void*) * p32.size());
+  // gather lists: entries (t, s), s > t, collected by s
+  std::vector<int> gcnt(op.nrows + 1, 0);
+  for (int t = 0; t < op.nrows; ++t)
+    for (int e = H.rowptr[t]; e < H.rowptr[t + 1]; ++e)
+      if (H.col[e] != t) gcnt[H.col[e] + 1]++;
+  for (int i = 0; i < op.nrows; ++i) gcnt[i + 1] += gcnt[i];
+  std::vector<int> gent(std::max(gcnt[op.nrows], 1)), fill(gcnt.begin(), gcnt.end() - 1);
+  for (int t = 0; t < op.nrows; ++t)
+    for (int e = H.rowptr[t]; e < H.rowptr[t + 1]; ++e)
+      if (H.col[e] != t) gent[fill[H.col[e]]++] = e;
+  op.gptr = (int*)up(gcnt.data(), sizeof(int) * gcnt.size());
+  op.gent = (int*)up(gent.data(), sizeof(int) * gent.size());
+  return op;
+}
+
+// Coupling rows of levels t*..top (+ the P_i blocks of level top when i >= 2).
+static OpHost coupling_rows(const Matrix& M, int top, int i) {
+  OpHost H;
+  H.rowptr.push_back(0);
+  for (int ell = M.tstar; ell <= top; ++ell) {
+    const HostCSR& F = M.far[ell];
+    auto ubF = ubase(F, 1 << ell, true);
+    const HostCSR* Ip = (i >= 2 && ell == top) ? &M.inadm[ell] : nullptr;
+    std::vector<int64_t> ubI;
+    if (Ip) ubI = ubase(*Ip, 1 << ell, false);
+    for (int t = 0; t < (1 << ell); ++t) {
+      // merge far (strict upper) and close (upper incl. diagonal) columns
+      std::vector<std::pair<int, std::pair<int, int64_t>>> ent;
+      for (int e = F.rowptr[t]; e < F.rowptr[t + 1]; ++e)
+        if (F.col[e] > t)
+          ent.push_back({F.col[e], {0, M.s_level_base[ell] + ubF[t] + upper_pos(F, t, F.col[e], true)}});
+      if (Ip)
+        for (int e = Ip->rowptr[t]; e < Ip->rowptr[t + 1]; ++e)
+          if (Ip->col[e] >= t) ent.push_back({Ip->col[e], {1, ubI[t] + upper_pos(*Ip, t, Ip->col[e], false)}});
+      std::sort(ent.begin(), ent.end());
+      for (auto& en : ent) {
+        H.col.push_back(M.slot0(ell) + en.first);
+        H.pool.push_back(en.second.first);
+        H.blk.push_back(en.second.second);
+      }
+      H.rowptr.push_back((int)H.col.size());
+    }
+  }
+  return H;
+}
+
+void setup_operators(Matrix& M) {
+  cudaStream_t s = M.stream;
+  const int L = M.L;
+  // close part of level 1
+  {
+    OpHost H;
+    const HostCSR& N = M.inadm[L];
+    H.rowptr.push_back(0);
+    int64_t b = 0;
+    for (int t = 0; t < (1 << L); ++t) {
+      for (int e = N.rowptr[t]; e < N.rowptr[t + 1]; ++e)
+        if (N.col[e] >= t) {
+          H.col.push_back(N.col[e]);
+          H.blk.push_back(b++);
+          H.pool.push_back(0);
+        }
+      H.rowptr.push_back((int)H.col.size());
+    }
+    M.opD = upload_op(M, H, M.KD, M.poolD.p, nullptr, M.poolD32.p, nullptr);
+  }
+  M.opC.assign(M.lev + 1, SymOp{});
+  size_t zmax = (size_t)M.opD.nnz * M.KD;
+  if (M.tstar >= 0) {
+    for (int i = 1; i <= M.lev; ++i) {
+      if (M.apply_only && i > 1) break;
+      int top = (i == 1) ? L : L - i + 2;
+      OpHost H = coupling_rows(M, top, i);
+      const void* pP = (i >= 2) ? M.poolP[i].p : nullptr;
+      const void* pP32 = (i >= 2 && M.with_f32) ? M.poolP32[i].p : nullptr;
+      M.opC[i] = upload_op(M, H, M.KC, M.poolS.p, pP, M.with_f32 ? M.poolS32.p : nullptr, pP32);
+      size_t zi = (size_t)M.opC[i].nnz * M.KC + (i == 1 ? (size_t)M.opD.nnz * M.KD : 0);
+      zmax = std::max(zmax, zi);
+    }
+    // transposed copies of the transfers and leaf bases (coalesced upward pass)
+    size_t nu = (size_t)(1 << L), ne = (size_t)M.nslots();
+    double* UT = (double*)M.alloc(sizeof(double) * nu * M.KD * M.KC);
+    double* ET = (double*)M.alloc(sizeof(double) * ne * M.KC * M.KC);
+    k_transpose_blocks<<<(int)nu, 256, 0, s>>>(M.d_U, M.KD, M.KC, UT);
+    k_transpose_blocks<<<(int)ne, 256, 0, s>>>(M.d_E, M.KC, M.KC, ET);
+    H2_LAUNCH_CHECK();
+    M.d_UT = UT;
+    M.d_ET = ET;
+    if (M.with_f32) {
+      float* UT32 = (float*)M.alloc(sizeof(float) * nu * M.KD * M.KC);
+      float* ET32 = (float*)M.alloc(sizeof(float) * ne * M.KC * M.KC);
+      k_transpose_blocks32<<<(int)nu, 256, 0, s>>>(M.d_U32, M.KD, M.KC, UT32);
+      k_transpose_blocks32<<<(int)ne, 256, 0, s>>>(M.d_E32, M.KC, M.KC, ET32);
+      H2_LAUNCH_CHECK();
+      M.d_UT32 = UT32;
+      M.d_ET32 = ET32;
+    }
+  }
+  size_t ncoef = (size_t)std::max(M.nslots(), 1) * M.KC;
+  size_t npts = (size_t)(1 << L) * M.KD;
+  M.wx.p = M.alloc(8 * ncoef);
+  M.wyrow.p = M.alloc(8 * ncoef);
+  M.wyc.p = M.alloc(8 * ncoef);
+  M.wxp.p = M.alloc(8 * npts);
+  M.wyp.p = M.alloc(8 * npts);
+  M.wz.bytes = 8 * std::max<size_t>(zmax, 1);
+  M.wz.p = M.alloc(M.wz.bytes);
+  H2_CUDA(cudaStreamSynchronize(s));
+}
+
+template <int FMT>
+static void launch_bsgemv(const SymOp& op, bool f32, const void* x, void* yrow, void* z, cudaStream_t s) {
+  using vt = typename Ar<FMT>::vec_t;
+  if (op.nrows == 0) return;
+  const void* const* blk = f32 ? op.blk32 : op.blk;
+  switch (op.K) {
+    case 16:
+      k_bsgemv<16, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z);
+      break;
+    case 32:
+      k_bsgemv<32, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z);
+      break;
+    case 64:
+      k_bsgemv<64, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z);
+      break;
+    default:
+      throw Error{H2MG_ERR_UNSUPPORTED, "block size not supported"};
+  }
+  H2_LAUNCH_CHECK();
+}
+
+template <int FMT, class BT>
+static void apply_impl(Matrix& M, int i, const double* x, double* y, cudaStream_t s, const BT* U,
+                       const BT* UT, const BT* E, const BT* ET) {
+  using vt = typename Ar<FMT>::vec_t;
+  const int L = M.L, KC = M.KC, KD = M.KD, ts = M.tstar;
+  const bool f32 = (FMT == FMT_F32);
+  vt* xc = (vt*)M.wx.p;
+  vt* yr = (vt*)M.wyrow.p;
+  vt* yc = (vt*)M.wyc.p;
+  vt* z = (vt*)M.wz.p;
+  if (i == 1) {
+    vt* xp = (vt*)M.wxp.p;
+    vt* yp = (vt*)M.wyp.p;
+    k_pts_in<FMT><<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, xp);
+    H2_LAUNCH_CHECK();
+    vt* zc = z + (size_t)M.opD.nnz * KD;
+    if (ts >= 0) {
+      k_up_leaf<FMT, BT><<<1 << L, std::max(KC, 32), 0, s>>>(UT, KD, KC, xp, xc + (size_t)M.slot0(L) * KC);
+      for (int ell = L - 1; ell >= ts; --ell)
+        k_up<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(ET + (size_t)M.slot0(ell + 1) * KC * KC, KC,
+                                                            xc + (size_t)M.slot0(ell + 1) * KC,
+                                                            xc + (size_t)M.slot0(ell) * KC);
+      H2_LAUNCH_CHECK();
+    }
+    launch_bsgemv<FMT>(M.opD, f32, xp, yp, z, s);
+    if (ts >= 0) {
+      launch_bsgemv<FMT>(M.opC[1], f32, xc, yr, zc, s);
+      for (int ell = ts; ell <= L; ++ell)
+        k_down_final<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(
+            M.slot0(ell), KC, yr, M.opC[1].gptr, M.opC[1].gent, zc,
+            ell > ts ? E + (size_t)M.slot0(ell) * KC * KC : nullptr,
+            ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, nullptr);
+      H2_LAUNCH_CHECK();
+    }
+    k_leaf_final<FMT, BT><<<1 << L, std::max(KD, 32), 0, s>>>(
+        KD, KC, yp, M.opD.gptr, M.opD.gent, z, ts >= 0 ? U : nullptr,
+        ts >= 0 ? yc + (size_t)M.slot0(L) * KC : nullptr, M.d_leafoff, M.d_perm, y);
+    H2_LAUNCH_CHECK();
+    return;
+  }
+  const int m = L - i + 2;
+  const int64_t nm = (int64_t)(1 << m) * KC;
+  k_coef_in<FMT><<<ceil_div(nm, 256), 256, 0, s>>>(x, nm, xc + (size_t)M.slot0(m) * KC);
+  H2_LAUNCH_CHECK();
+  for (int ell = m - 1; ell >= ts; --ell)
+    k_up<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(ET + (size_t)M.slot0(ell + 1) * KC * KC, KC,
+                                                        xc + (size_t)M.slot0(ell + 1) * KC,
+                                                        xc + (size_t)M.slot0(ell) * KC);
+  H2_LAUNCH_CHECK();
+  launch_bsgemv<FMT>(M.opC[i], f32, xc, yr, z, s);
+  for (int ell = ts; ell <= m; ++ell)
+    k_down_final<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(
+        M.slot0(ell), KC, yr, M.opC[i].gptr, M.opC[i].gent, z,
+        ell > ts ? E + (size_t)M.slot0(ell) * KC * KC : nullptr,
+        ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, ell == m ? y : nullptr);
+  H2_LAUNCH_CHECK();
+}
+
+void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s) {
+  if (f32) {
+    H2_REQUIRE(M.with_f32, H2MG_ERR_INVALID_ARG, "matrix was built without an FP32 copy");
+    apply_impl<FMT_F32, float>(M, i, x, y, s, M.d_U32, M.d_UT32, M.d_E32, M.d_ET32);
+  } else if (M.fmt == FMT_DF) {
+    apply_impl<FMT_DF, double>(M, i, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET);
+  } else {
+    apply_impl<FMT_F64, double>(M, i, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET);
+  }
+}
+
+// Algorithmic bytes of one A_i apply in the primary format: every stored block once,
+// the transfers (and leaf bases at i = 1) twice, the input and output vectors once.
+int64_t apply_bytes(const Matrix& M, int i) {
+  int64_t eb = fmt_bytes(M.fmt);
+  int64_t bytes = 0;
+  if (i == 1) {
+    bytes += (int64_t)M.opD.nnz * M.KD * M.KD * eb + 2 * 8 * M.n;
+    if (M.tstar >= 0) {
+      bytes += (int64_t)M.opC[1].nnz * M.KC * M.KC * eb;
+      bytes += 2 * 8 * ((int64_t)(1 << M.L) * M.KD * M.KC);
+      for (int ell = M.tstar + 1; ell <= M.L; ++ell) bytes += 2 * 8 * ((int64_t)(1 << ell) * M.KC * M.KC);
+    }
+    return bytes;
+  }
+  int m = M.L - i + 2;
+  bytes += (int64_t)M.opC[i].nnz * M.KC * M.KC * eb + 2 * 8 * ((int64_t)(1 << m) * M.KC);
+  for (int ell = M.tstar + 1; ell <= m; ++ell) bytes += 2 * 8 * ((int64_t)(1 << ell) * M.KC * M.KC);
+  return bytes;
+}
+
+}  // namespace h2mg

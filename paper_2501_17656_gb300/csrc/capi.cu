@@ -1,0 +1,443 @@
+// capi.cu -- the extern "C" entry points declared in include/h2mg.h.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace h2mg {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+void* Matrix::alloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 8;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{e == cudaErrorMemoryAllocation ? H2MG_ERR_OOM : H2MG_ERR_CUDA,
+                "cudaMalloc(" + std::to_string(bytes) + " B): " + cudaGetErrorString(e)};
+  }
+  owned.push_back({p, bytes});
+  e = cudaMemsetAsync(p, 0, bytes, stream);
+  if (e != cudaSuccess) throw Error{H2MG_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)};
+  return p;
+}
+
+Matrix::~Matrix() {
+  if (stream) cudaStreamSynchronize(stream);
+  for (auto& d : owned)
+    if (d.p) cudaFree(d.p);
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A device view of a caller buffer: the buffer itself, or a staged copy.
+struct DevView {
+  double* d = nullptr;
+  bool staged = false;
+  DevView(const double* p, int64_t n, bool copy_in, cudaStream_t s) {
+    if (p == nullptr) return;
+    if (is_device_ptr(p)) {
+      d = const_cast<double*>(p);
+    } else {
+      staged = true;
+      H2_CUDA(cudaMalloc(&d, sizeof(double) * std::max<int64_t>(n, 1)));
+      if (copy_in) H2_CUDA(cudaMemcpyAsync(d, p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    }
+  }
+  void copy_out(double* host, int64_t n, cudaStream_t s) {
+    if (staged) {
+      H2_CUDA(cudaMemcpyAsync(host, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+      H2_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  ~DevView() {
+    if (staged && d) cudaFree(d);
+  }
+};
+
+__global__ void k_point_weights(const int* __restrict__ perm, int64_t n, int dim, const double* __restrict__ Xt,
+                                const double* __restrict__ w, const double* __restrict__ dg, KernelParams kp,
+                                double* __restrict__ sw, double* __restrict__ dgo) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int i = perm[p];
+  double wi = w ? w[i] : 1.0;
+  sw[p] = sqrt(wi);
+  double d = dg ? dg[i] : wi * kernel_self(kp, Xt + p * dim, dim);
+  dgo[p] = d + kp.nugget;
+}
+
+__global__ void k_check_pos(const double* __restrict__ v, int64_t n, int* __restrict__ flag) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !(v[i] > 0.0 && isfinite(v[i]))) atomicOr(flag, 2);
+}
+
+static int pad_dim(int v) { return v <= 16 ? 16 : v <= 32 ? 32 : 64; }
+
+static void build_all(Matrix& M, const double* points, const h2mg_kernel* k, const h2mg_build_opts* o) {
+  cudaStream_t s = M.stream;
+  M.d_flag = (int*)M.alloc(sizeof(int) * 4);
+  DevView P(points, M.n * M.dim, true, s);
+  build_tree(M, P.d);
+  // weights and diagonal in tree order
+  {
+    DevView W(k->weights, k->weights ? M.n : 0, true, s);
+    DevView G(k->diag, k->diag ? M.n : 0, true, s);
+    if (k->weights) {
+      H2_CUDA(cudaMemsetAsync(M.d_flag, 0, sizeof(int), s));
+      k_check_pos<<<ceil_div(M.n, 256), 256, 0, s>>>(W.d, M.n, M.d_flag);
+      int h = 0;
+      H2_CUDA(cudaMemcpyAsync(&h, M.d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      H2_CUDA(cudaStreamSynchronize(s));
+      H2_REQUIRE(h == 0, H2MG_ERR_INVALID_ARG, "weights must be positive and finite");
+    }
+    M.d_sw = (double*)M.alloc(sizeof(double) * M.n);
+    M.d_dg = (double*)M.alloc(sizeof(double) * M.n);
+    k_point_weights<<<ceil_div(M.n, 256), 256, 0, s>>>(M.d_perm, M.n, M.dim, M.d_X, k->weights ? W.d : nullptr,
+                                                       k->diag ? G.d : nullptr, M.kp, M.d_sw, M.d_dg);
+    H2_LAUNCH_CHECK();
+    H2_CUDA(cudaStreamSynchronize(s));
+  }
+  build_partition(M);
+  M.KC = pad_dim(M.k);
+  M.lev = o->coarse_level < 0 ? M.lev_nat : o->coarse_level;
+  H2_REQUIRE(M.lev >= 1 && M.lev <= M.lev_nat, H2MG_ERR_INVALID_ARG,
+             "coarse_level must be -1 or in [1, " + std::to_string(M.lev_nat) + "]");
+  if (M.apply_only) M.lev = std::min(M.lev, 1);
+  build_bases(M);
+  build_blocks(M, nullptr);
+  if (!M.apply_only) build_coarse_near(M);
+  build_f32_copies(M);
+  setup_operators(M);
+  if (!M.apply_only) build_dense_coarse(M);
+  H2_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace h2mg
+
+using namespace h2mg;
+
+struct h2mg_matrix_s {
+  Matrix M;
+};
+
+template <class F>
+static h2mg_status guard(F f) {
+  try {
+    g_last_error.clear();
+    return f();
+  } catch (const Error& e) {
+    set_error(e.msg);
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return H2MG_ERR_OOM;
+  } catch (...) {
+    set_error("unknown error");
+    return H2MG_ERR_CUDA;
+  }
+}
+
+extern "C" {
+
+const char* h2mg_error_string(h2mg_status s) {
+  switch (s) {
+    case H2MG_OK: return "success";
+    case H2MG_ERR_INVALID_ARG: return "invalid argument";
+    case H2MG_ERR_OOM: return "out of device memory";
+    case H2MG_ERR_CUDA: return "CUDA error";
+    case H2MG_ERR_NOT_SPD: return "coarse operator is not positive definite";
+    case H2MG_ERR_NOT_CONVERGED: return "not converged";
+    case H2MG_ERR_NAN: return "NaN or Inf encountered";
+    case H2MG_ERR_TIMEOUT: return "device wait timed out";
+    case H2MG_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* h2mg_last_error(void) { return g_last_error.c_str(); }
+
+h2mg_status h2mg_build(const double* points, int64_t n, int dim, const h2mg_kernel* k,
+                       const h2mg_build_opts* o, void* stream, h2mg_matrix* out) {
+  if (out) *out = nullptr;
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(out && points && k && o, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    H2_REQUIRE(n >= 1 && n <= (1ll << 30), H2MG_ERR_INVALID_ARG, "n must be in [1, 2^30]");
+    H2_REQUIRE(dim >= 1 && dim <= 3, H2MG_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
+    H2_REQUIRE(o->leaf_size >= 2 && o->leaf_size <= 64, H2MG_ERR_INVALID_ARG, "leaf_size must be in [2, 64]");
+    H2_REQUIRE(o->cheb_q >= 1, H2MG_ERR_INVALID_ARG, "cheb_q must be >= 1");
+    int kk = 1;
+    for (int d = 0; d < dim; ++d) kk *= o->cheb_q;
+    H2_REQUIRE(kk <= 64, H2MG_ERR_UNSUPPORTED, "rank q^dim must be <= 64");
+    H2_REQUIRE(o->eta >= 0.0 && std::isfinite(o->eta), H2MG_ERR_INVALID_ARG, "eta must be finite and >= 0");
+    H2_REQUIRE(o->storage == H2MG_STORE_F64 || o->storage == H2MG_STORE_DF64, H2MG_ERR_INVALID_ARG,
+               "storage must be H2MG_STORE_F64 or H2MG_STORE_DF64");
+    H2_REQUIRE(k->kind >= 0 && k->kind <= H2MG_K_DMATERN32_DL, H2MG_ERR_INVALID_ARG, "unknown kernel kind");
+    H2_REQUIRE(k->kind == H2MG_K_POLY || k->kind == H2MG_K_LAPLACE_SL || (k->length > 0 && std::isfinite(k->length)),
+               H2MG_ERR_INVALID_ARG, "length must be > 0");
+    H2_REQUIRE(k->kind != H2MG_K_POLY || (k->degree >= 0 && k->degree <= 16), H2MG_ERR_INVALID_ARG,
+               "degree must be in [0, 16]");
+    H2_REQUIRE(k->kind != H2MG_K_LAPLACE_SL || k->diag, H2MG_ERR_INVALID_ARG,
+               "the single-layer kernel needs a diagonal override");
+    H2_REQUIRE(std::isfinite(k->nugget), H2MG_ERR_INVALID_ARG, "nugget must be finite");
+    auto* h = new h2mg_matrix_s();
+    Matrix& M = h->M;
+    M.n = n;
+    M.dim = dim;
+    M.kp = KernelParams{k->kind, k->length, k->nugget, k->degree};
+    M.has_weights = k->weights != nullptr;
+    M.has_diag = k->diag != nullptr;
+    M.leaf = o->leaf_size;
+    M.q = o->cheb_q;
+    M.k = kk;
+    M.eta = o->eta;
+    M.fmt = o->storage == H2MG_STORE_DF64 ? FMT_DF : FMT_F64;
+    M.with_f32 = o->with_f32 != 0;
+    M.stream = (cudaStream_t)stream;
+    try {
+      build_all(M, points, k, o);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_destroy(h2mg_matrix A) {
+  return guard([&]() -> h2mg_status {
+    delete A;
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int64_t ld, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && x && y, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    H2_REQUIRE(nrhs >= 1 && ld >= M.n, H2MG_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= n");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int c = 0; c < nrhs; ++c) {
+      DevView X(x + (int64_t)c * ld, M.n, true, s), Y(y + (int64_t)c * ld, M.n, false, s);
+      apply_level(M, 1, false, X.d, Y.d, s);
+      Y.copy_out(y + (int64_t)c * ld, M.n, s);
+    }
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int64_t ld,
+                       const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && b && x && o, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    H2_REQUIRE(nrhs >= 1 && ld >= M.n, H2MG_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= n");
+    H2_REQUIRE(o->max_cycles >= 0 && o->n_f >= 0 && o->n_c >= 0 && o->tol >= 0, H2MG_ERR_INVALID_ARG,
+               "bad solve options");
+    H2_REQUIRE(o->precision == H2MG_PREC_F64 || (o->precision == H2MG_PREC_MIXED_F32 && M.with_f32),
+               H2MG_ERR_INVALID_ARG, "mixed precision needs a matrix built with_f32");
+    H2_REQUIRE(!M.apply_only, H2MG_ERR_INVALID_ARG, "matrix was built for products only");
+    if (!M.coarse_ok) throw Error{H2MG_ERR_NOT_SPD, "the coarsest operator is not positive definite"};
+    cudaStream_t s = (cudaStream_t)stream;
+    h2mg_status worst = H2MG_OK;
+    for (int c = 0; c < nrhs; ++c) {
+      DevView B(b + (int64_t)c * ld, M.n, true, s), X(x + (int64_t)c * ld, M.n, true, s);
+      h2mg_status st = solve(M, B.d, X.d, *o, info, s);
+      X.copy_out(x + (int64_t)c * ld, M.n, s);
+      if (st != H2MG_OK && worst == H2MG_OK) worst = st;
+    }
+    if (worst != H2MG_OK) set_error(h2mg_error_string(worst));
+    return worst;
+  });
+}
+
+h2mg_status h2mg_query(h2mg_matrix A, int what, int arg, int64_t* value) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && value, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    int64_t v = 0;
+    switch (what) {
+      case H2MG_Q_N: v = M.n; break;
+      case H2MG_Q_DIM: v = M.dim; break;
+      case H2MG_Q_L: v = M.L; break;
+      case H2MG_Q_TSTAR: v = M.tstar; break;
+      case H2MG_Q_LEVELS: v = M.lev; break;
+      case H2MG_Q_KD: v = M.KD; break;
+      case H2MG_Q_KC: v = M.KC; break;
+      case H2MG_Q_RANK: v = M.k; break;
+      case H2MG_Q_NEAR_PAIRS: v = M.nD; break;
+      case H2MG_Q_FAR_PAIRS: {
+        H2_REQUIRE(arg >= 0 && arg <= M.L, H2MG_ERR_INVALID_ARG, "level out of range");
+        const HostCSR& F = M.far[arg];
+        for (int t = 0; t + 1 < (int)F.rowptr.size(); ++t)
+          for (int e = F.rowptr[t]; e < F.rowptr[t + 1]; ++e) v += F.col[e] > t;
+        break;
+      }
+      case H2MG_Q_LEVEL_SIZE:
+        H2_REQUIRE(arg >= 1 && arg <= M.lev, H2MG_ERR_INVALID_ARG, "level out of range");
+        v = level_size(M, arg);
+        break;
+      case H2MG_Q_BYTES_PRIMARY: {
+        v = M.poolD.bytes + M.poolS.bytes;
+        for (auto& p : M.poolP) v += p.bytes;
+        break;
+      }
+      case H2MG_Q_BYTES_F32: {
+        v = M.poolD32.bytes + M.poolS32.bytes;
+        for (auto& p : M.poolP32) v += p.bytes;
+        break;
+      }
+      case H2MG_Q_APPLY_BYTES:
+        H2_REQUIRE(arg >= 1 && arg <= M.lev, H2MG_ERR_INVALID_ARG, "level out of range");
+        v = apply_bytes(M, arg);
+        break;
+      case H2MG_Q_DEVICE_BYTES:
+        for (auto& d : M.owned) v += d.bytes;
+        break;
+      default:
+        throw Error{H2MG_ERR_INVALID_ARG, "unknown query"};
+    }
+    *value = v;
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_export(h2mg_matrix A, int what, int arg, void* buf, int64_t cap, int64_t* bytes) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && bytes, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    std::vector<char> out;
+    auto put_ints = [&](const std::vector<int>& v) {
+      out.resize(v.size() * sizeof(int));
+      if (!v.empty()) memcpy(out.data(), v.data(), out.size());
+    };
+    switch (what) {
+      case H2MG_X_PERM: {
+        std::vector<int> v(M.n);
+        H2_CUDA(cudaMemcpy(v.data(), M.d_perm, sizeof(int) * M.n, cudaMemcpyDeviceToHost));
+        put_ints(v);
+        break;
+      }
+      case H2MG_X_LEAF_OFFSETS:
+        put_ints(M.offsets[M.L]);
+        break;
+      case H2MG_X_NEAR:
+      case H2MG_X_FAR: {
+        int ell = what == H2MG_X_NEAR ? M.L : arg;
+        H2_REQUIRE(ell >= 0 && ell <= M.L, H2MG_ERR_INVALID_ARG, "level out of range");
+        const HostCSR& C = what == H2MG_X_NEAR ? M.inadm[M.L] : M.far[ell];
+        std::vector<int> v;
+        for (int t = 0; t + 1 < (int)C.rowptr.size(); ++t)
+          for (int e = C.rowptr[t]; e < C.rowptr[t + 1]; ++e)
+            if (what == H2MG_X_NEAR ? C.col[e] >= t : C.col[e] > t) {
+              v.push_back(t);
+              v.push_back(C.col[e]);
+            }
+        put_ints(v);
+        break;
+      }
+      case H2MG_X_RANKS: {
+        H2_REQUIRE(M.tstar >= 0 && arg >= M.tstar && arg <= M.L, H2MG_ERR_INVALID_ARG, "level has no basis");
+        std::vector<int> v(M.h_rank.begin() + M.slot0(arg), M.h_rank.begin() + M.slot0(arg) + (1 << arg));
+        put_ints(v);
+        break;
+      }
+      case H2MG_X_BOXES: {
+        H2_REQUIRE(arg >= 0 && arg <= M.L, H2MG_ERR_INVALID_ARG, "level out of range");
+        size_t nb = sizeof(double) * 2 * M.dim * (1 << arg);
+        out.resize(nb);
+        H2_CUDA(cudaMemcpy(out.data(), M.d_box[arg], nb, cudaMemcpyDeviceToHost));
+        break;
+      }
+      default:
+        throw Error{H2MG_ERR_INVALID_ARG, "unknown export"};
+    }
+    *bytes = (int64_t)out.size();
+    if (buf && cap >= (int64_t)out.size() && !out.empty()) memcpy(buf, out.data(), out.size());
+    else if (buf && cap < (int64_t)out.size()) throw Error{H2MG_ERR_INVALID_ARG, "buffer too small"};
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_apply_level(h2mg_matrix A, int level, int precision, const double* x, double* y,
+                             void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && x && y, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    H2_REQUIRE(level >= 1 && level <= M.lev, H2MG_ERR_INVALID_ARG, "level out of range");
+    H2_REQUIRE(precision == H2MG_PREC_F64 || (precision == H2MG_PREC_MIXED_F32 && M.with_f32),
+               H2MG_ERR_INVALID_ARG, "no FP32 copy");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n = level_size(M, level);
+    DevView X(x, n, true, s), Y(y, n, false, s);
+    apply_level(M, level, precision == H2MG_PREC_MIXED_F32, X.d, Y.d, s);
+    Y.copy_out(y, n, s);
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_coarse_solve(h2mg_matrix A, const double* r, double* e, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && r && e, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    H2_REQUIRE(!M.apply_only, H2MG_ERR_INVALID_ARG, "matrix was built for products only");
+    if (!M.coarse_ok) throw Error{H2MG_ERR_NOT_SPD, "the coarsest operator is not positive definite"};
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n = level_size(M, M.lev);
+    DevView R(r, n, true, s), E(e, n, false, s);
+    coarse_solve(M, R.d, E.d, s);
+    E.copy_out(e, n, s);
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_smooth(h2mg_matrix A, int level, int precision, const double* f, const double* x0, int n,
+                        double* x, double* r, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && f && x && n >= 0, H2MG_ERR_INVALID_ARG, "bad argument");
+    Matrix& M = A->M;
+    H2_REQUIRE(level >= 1 && level <= M.lev, H2MG_ERR_INVALID_ARG, "level out of range");
+    H2_REQUIRE(precision == H2MG_PREC_F64 || (precision == H2MG_PREC_MIXED_F32 && M.with_f32),
+               H2MG_ERR_INVALID_ARG, "no FP32 copy");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t N = level_size(M, level);
+    DevView F(f, N, true, s), X(x, N, false, s);
+    DevView X0(x0 ? x0 : f, x0 ? N : 0, x0 != nullptr, s);
+    DevView R(r ? r : x, N, false, s);
+    smooth(M, level, precision == H2MG_PREC_MIXED_F32, F.d, x0 ? X0.d : nullptr, n, X.d, r ? R.d : nullptr, s);
+    X.copy_out(x, N, s);
+    if (r) R.copy_out(r, N, s);
+    H2_CUDA(cudaStreamSynchronize(s));
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_vcycle(h2mg_matrix A, const double* x0, const double* r1, double* x_out,
+                        const h2mg_solve_opts* o, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && x0 && r1 && x_out && o, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    H2_REQUIRE(!M.apply_only, H2MG_ERR_INVALID_ARG, "matrix was built for products only");
+    if (!M.coarse_ok) throw Error{H2MG_ERR_NOT_SPD, "the coarsest operator is not positive definite"};
+    cudaStream_t s = (cudaStream_t)stream;
+    DevView X0(x0, M.n, true, s), R(r1, M.n, true, s), X(x_out, M.n, false, s);
+    vcycle(M, *o, X0.d, R.d, X.d, s);
+    X.copy_out(x_out, M.n, s);
+    H2_CUDA(cudaStreamSynchronize(s));
+    return H2MG_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// internal.h -- handle layout and internal entry points of the H2-MG library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace h2mg {
+
+// Device allocation owned by a handle; freed by the handle's destructor.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// A symmetric block-sparse operator over one index space of "slots" (clusters),
+// stored as its upper triangle: row t holds entries (t, s) with s >= t. Each
+// entry points at a K x K block in some pool (swizzled layout, see swz). The
+// transposed product of entry (t, s), s > t, is written to the entry's scratch
+// row and gathered for row s by `gptr/gent`.
+struct SymOp {
+  int K = 0;
+  int nrows = 0;          // slots
+  int nnz = 0;            // stored entries
+  int* rowptr = nullptr;  // [nrows + 1]
+  int* col = nullptr;     // [nnz]
+  const void** blk = nullptr;      // [nnz] block pointers into the primary pool
+  const void** blk32 = nullptr;    // [nnz] block pointers into the FP32 pool (or null)
+  int* gptr = nullptr;    // [nrows + 1] gather lists
+  int* gent = nullptr;    // entries e with col[e] == row and row(e) < col[e]
+};
+
+// Host-side copy of a full (both triangles) CSR list of cluster pairs.
+struct HostCSR {
+  std::vector<int> rowptr, col;
+  int nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
+};
+
+struct Matrix {
+  // ---- problem
+  int64_t n = 0;
+  int dim = 0;
+  KernelParams kp{};
+  bool has_weights = false, has_diag = false;
+  int leaf = 0, q = 0, k = 0;
+  double eta = 0;
+  int fmt = FMT_F64;      // primary block format (FMT_F64 or FMT_DF)
+  bool with_f32 = false;
+  bool apply_only = false;
+  cudaStream_t stream = nullptr;
+
+  // ---- tree (tree order = leaf-major, padded to KD slots per leaf)
+  int L = 0;              // leaf depth
+  int KD = 0, KC = 0;     // padded leaf size and padded rank
+  int tstar = -1;         // first level with a far pair (-1: none)
+  int lev_nat = 1, lev = 1;  // natural and chosen coarsest multigrid level l
+  std::vector<std::vector<int>> offsets;  // per level, cluster offsets in compact tree order
+  int* d_perm = nullptr;       // [n] original index of compact tree position
+  int* d_slot_of = nullptr;    // [n] padded slot of each original index
+  int* d_leafoff = nullptr;    // [2^L + 1] compact offsets of the leaves
+  double* d_X = nullptr;       // [n * dim] points in compact tree order
+  double* d_sw = nullptr;      // [n] sqrt(w) in compact tree order
+  double* d_dg = nullptr;      // [n] diagonal entries A_ii in compact tree order
+  std::vector<double*> d_box;  // per level, [2^ell * 2 * dim] (lo, hi)
+  double* d_nodes = nullptr;   // Chebyshev nodes of clusters at levels tstar..L (heap slots)
+  int* d_rank = nullptr;       // ranks per slot (levels tstar..L)
+  std::vector<int> h_rank;     // host copy
+
+  // ---- partition (host copies, full lists per level)
+  std::vector<HostCSR> far, inadm;
+
+  // ---- bases (float64, natural column-major, padded)
+  double* d_U = nullptr;       // [2^L][KD x KC]
+  double* d_E = nullptr;       // per slot at levels tstar+1..L: [KC x KC] (child -> parent transfer)
+  double* d_R = nullptr;       // per slot at levels tstar..L: [KC x KC] (rows >= rank are zero)
+  float* d_U32 = nullptr;
+  float* d_E32 = nullptr;
+  double* d_UT = nullptr;      // transposes (KC x KD per leaf, KC x KC per slot)
+  double* d_ET = nullptr;
+  float* d_UT32 = nullptr;
+  float* d_ET32 = nullptr;
+
+  // ---- block pools (primary format and optional FP32 copy)
+  DevBuf poolD, poolS, poolD32, poolS32;
+  std::vector<DevBuf> poolP, poolP32;         // index = multigrid level i (2..lev)
+  int64_t nD = 0, nS = 0;                     // stored blocks
+  std::vector<int64_t> nP;
+  std::vector<int64_t> s_level_base;          // first S block of each level (index ell)
+
+  // ---- operators
+  SymOp opD;                    // level 1 close part (KD, point slots = leaves)
+  std::vector<SymOp> opC;       // index i: coupling (+ P_i) operator of multigrid level i
+  int slot0(int ell) const { return (1 << ell) - (1 << tstar); }   // first coef slot of level ell
+  int nslots() const { return tstar < 0 ? 0 : (1 << (L + 1)) - (1 << tstar); }
+
+  // ---- dense coarsest operator and Cholesky factor
+  int nl = 0;                   // size of A_l
+  double* d_Al = nullptr;       // [nl * nl] column-major; lower triangle holds the factor
+  bool coarse_ok = false;
+
+  // ---- workspaces
+  DevBuf wx, wyrow, wyc;        // coefficient buffers (nslots * KC elements, 8 B)
+  DevBuf wxp, wyp;              // point buffers (2^L * KD elements, 8 B)
+  DevBuf wz;                    // scratch for transposed products
+  DevBuf wstage;                // host staging
+  DevBuf wvec;                  // multigrid vectors (float64)
+  DevBuf wred;                  // reduction partials + scalars
+  DevBuf wcoarse;               // two vectors of the coarse size (triangular solves)
+  int* d_flag = nullptr;        // device error flags
+
+  std::vector<DevBuf> owned;    // everything else
+  ~Matrix();
+  void* alloc(size_t bytes);    // owned allocation, zero-initialised
+};
+
+// ---- tree.cu
+void build_tree(Matrix& M, const double* d_points_user);
+void build_partition(Matrix& M);
+// ---- fill.cu
+void build_bases(Matrix& M);
+void build_blocks(Matrix& M, const Matrix* base);
+void build_coarse_near(Matrix& M);
+void build_f32_copies(Matrix& M);
+// ---- dense.cu
+void build_dense_coarse(Matrix& M);
+void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s);
+// ---- apply.cu
+void setup_operators(Matrix& M);
+void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s);
+int64_t apply_bytes(const Matrix& M, int i);
+// ---- solve.cu
+void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n, double* x,
+            double* r, cudaStream_t s);
+void restrict_level(Matrix& M, int i, const double* v, double* out, cudaStream_t s);
+void prolong_add(Matrix& M, int i, const double* e, double* out, cudaStream_t s);
+void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double* r1, double* xout,
+            cudaStream_t s);
+h2mg_status solve(Matrix& M, const double* b, double* x, const h2mg_solve_opts& o,
+                  h2mg_solve_info* info, cudaStream_t s);
+int64_t level_size(const Matrix& M, int i);
+
+// ---- sort.cu (device primitives)
+void exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, Matrix& M);
+void radix_sort_u64(uint64_t* keys, int* vals, int n, int bits, Matrix& M, cudaStream_t s);
+
+}  // namespace h2mg
