@@ -190,9 +190,29 @@ h2mg_status h2mg_coarse_solve(h2mg_matrix A, const double* r, double* e, void* s
 h2mg_status h2mg_smooth(h2mg_matrix A, int level, int precision, const double* f,
                         const double* x0, int n, double* x, double* r, void* stream);
 
+/* Inter-level transfer of Algorithm 1 (Sec. 3.3): direction 0 = restriction
+ * out = U_i^T v (level i -> level i+1), direction 1 = prolongation out = U_i v
+ * (level i+1 -> level i; out is overwritten). Vectors as for h2mg_apply_level. */
+h2mg_status h2mg_transfer(h2mg_matrix A, int level, int direction, const double* v, double* out,
+                          void* stream);
+
 /* One V-cycle (Algorithm 1) from x0 with r1 = b - A x0 given: x_out = x0 + e_1. */
 h2mg_status h2mg_vcycle(h2mg_matrix A, const double* x0, const double* r1, double* x_out,
                         const h2mg_solve_opts* o, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process so far (all
+ * handles, all threads). Callers difference two readings to count the launches of a
+ * region of work. */
+int64_t h2mg_launch_count(void);
+
+/* Timing of the symmetric block-sparse product (the kernel that streams the stored
+ * blocks D, S and P_i). enable = 1 clears the record and starts recording a pair of
+ * CUDA events around each of its launches on the launching stream; enable = 0 stops.
+ * On every call *launches, *ms (sum of the launch durations) and *bytes (sum of the
+ * algorithmic bytes: stored blocks, input and output vectors, transposed partials)
+ * are returned for the record so far; reading synchronises the recorded events.
+ * Any output pointer may be NULL. */
+h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* ms, double* bytes);
 
 #ifdef __cplusplus
 }

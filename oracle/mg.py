@@ -247,6 +247,45 @@ def solve(mg: H2MG, b: np.ndarray, opts: SolveOpts, x0: np.ndarray | None = None
     return x, info
 
 
+def solve_fcg(mg: H2MG, b: np.ndarray, opts: SolveOpts, low=None):
+    """Flexible CG preconditioned by one V-cycle (multigrid used to precondition
+    another iteration, Section 3.2). The V-cycle with CG smoothers is a nonlinear
+    map, so each new direction is made A-orthogonal to the previous one (flexible
+    CG with one stored direction). The residual is recomputed explicitly in float64
+    each iteration; ``low`` runs the V-cycle on rounded operators as in
+    ``solve_mixed``. ``cycles`` counts V-cycles."""
+    ops = None if low is None else LowPrecisionOps(mg, low)
+    x = np.zeros_like(b)
+    nb = float(np.linalg.norm(b))
+    info = SolveInfo()
+    p_prev = q_prev = None
+    for cyc in range(opts.max_cycles + 1):
+        r = b - mg.apply(1, x)
+        rel = float(np.linalg.norm(r)) / nb if nb > 0 else 0.0
+        info.history.append(rel)
+        info.cycles, info.relres = cyc, rel
+        if rel <= opts.tol:
+            info.converged = True
+            break
+        if cyc == opts.max_cycles:
+            break
+        if ops is None:
+            z = vcycle(mg, np.zeros_like(r), r, opts)
+        else:
+            rl = r.astype(low)
+            z = vcycle(mg, np.zeros_like(rl), rl, opts, ops=ops).astype(np.float64)
+        if p_prev is None:
+            p = z
+        else:
+            beta = -float(z @ q_prev) / float(p_prev @ q_prev)
+            p = z + beta * p_prev
+        q = mg.apply(1, p)
+        alpha = float(p @ r) / float(p @ q)
+        x = x + alpha * p
+        p_prev, q_prev = p, q
+    return x, info
+
+
 def solve_mixed(mg: H2MG, b: np.ndarray, opts: SolveOpts, low=np.float32):
     """Iterative refinement: float64 residual and update around a V-cycle whose
     operators and vectors are rounded to ``low`` (the coarse solve stays float64)."""

@@ -34,7 +34,8 @@ X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5)
 
 EXPORTED = ["h2mg_build", "h2mg_apply", "h2mg_solve", "h2mg_destroy", "h2mg_error_string",
             "h2mg_last_error", "h2mg_query", "h2mg_export", "h2mg_apply_level",
-            "h2mg_coarse_solve", "h2mg_smooth", "h2mg_vcycle"]
+            "h2mg_coarse_solve", "h2mg_smooth", "h2mg_vcycle", "h2mg_launch_count", "h2mg_profile",
+            "h2mg_transfer"]
 
 
 class H2MGError(RuntimeError):
@@ -100,9 +101,13 @@ def load_library(build_if_missing: bool = False):
     lib.h2mg_coarse_solve.argtypes = [vp, vp, vp, vp]
     lib.h2mg_smooth.argtypes = [vp, ci, ci, vp, vp, ci, vp, vp, vp]
     lib.h2mg_vcycle.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_SolveOpts), vp]
+    lib.h2mg_launch_count.argtypes = []
+    lib.h2mg_transfer.argtypes = [vp, ci, ci, vp, vp, vp]
+    lib.h2mg_profile.argtypes = [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(cd), ctypes.POINTER(cd)]
     for name in EXPORTED:
-        if name not in ("h2mg_error_string", "h2mg_last_error"):
+        if name not in ("h2mg_error_string", "h2mg_last_error", "h2mg_launch_count"):
             getattr(lib, name).restype = ci
+    lib.h2mg_launch_count.restype = i64
     _lib = lib
     return lib
 
@@ -196,6 +201,17 @@ class H2Matrix:
         _check(self._lib.h2mg_export(self._h, X[what], int(arg), buf.ctypes.data, buf.nbytes, ctypes.byref(nb)))
         return buf[: int(nb.value) // np.dtype(dtype).itemsize]
 
+    def profile(self, enable: int):
+        """Start (1) / stop (0) timing of the block-product launches; returns
+        (launches, ms, bytes) recorded so far."""
+        n, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.h2mg_profile(self._h, int(enable), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+        return int(n.value), float(ms.value), float(by.value)
+
+    @staticmethod
+    def launch_count() -> int:
+        return int(load_library().h2mg_launch_count())
+
     @property
     def levels(self) -> int:
         return self.query("LEVELS")
@@ -218,6 +234,18 @@ class H2Matrix:
             y = _like(x, self.level_size(i))
         _check(self._lib.h2mg_apply_level(self._h, int(i), PRECISION[precision], _ptr(x), _ptr(y), _stream()))
         return y
+
+    def restrict(self, i: int, v):
+        """U_i^T v (level i -> i+1)."""
+        out = _like(v, self.level_size(i + 1))
+        _check(self._lib.h2mg_transfer(self._h, int(i), 0, _ptr(v), _ptr(out), _stream()))
+        return out
+
+    def prolong(self, i: int, e):
+        """U_i e (level i+1 -> i)."""
+        out = _like(e, self.level_size(i))
+        _check(self._lib.h2mg_transfer(self._h, int(i), 1, _ptr(e), _ptr(out), _stream()))
+        return out
 
     def coarse_solve(self, r, e=None):
         if e is None:

@@ -389,6 +389,7 @@ static SymOp upload_op(Matrix& M, const OpHost& H, int K, const void* pool0, con
   for (int t = 0; t < op.nrows; ++t)
     for (int e = H.rowptr[t]; e < H.rowptr[t + 1]; ++e)
       if (H.col[e] != t) gent[fill[H.col[e]]++] = e;
+  op.noff = gcnt[op.nrows];
   op.gptr = (int*)up(gcnt.data(), sizeof(int) * gcnt.size());
   op.gent = (int*)up(gent.data(), sizeof(int) * gent.size());
   return op;
@@ -462,16 +463,16 @@ void setup_operators(Matrix& M) {
     size_t nu = (size_t)(1 << L), ne = (size_t)M.nslots();
     double* UT = (double*)M.alloc(sizeof(double) * nu * M.KD * M.KC);
     double* ET = (double*)M.alloc(sizeof(double) * ne * M.KC * M.KC);
-    k_transpose_blocks<<<(int)nu, 256, 0, s>>>(M.d_U, M.KD, M.KC, UT);
-    k_transpose_blocks<<<(int)ne, 256, 0, s>>>(M.d_E, M.KC, M.KC, ET);
+    { k_transpose_blocks<<<(int)nu, 256, 0, s>>>(M.d_U, M.KD, M.KC, UT); ::h2mg::count_launch(); }
+    { k_transpose_blocks<<<(int)ne, 256, 0, s>>>(M.d_E, M.KC, M.KC, ET); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     M.d_UT = UT;
     M.d_ET = ET;
     if (M.with_f32) {
       float* UT32 = (float*)M.alloc(sizeof(float) * nu * M.KD * M.KC);
       float* ET32 = (float*)M.alloc(sizeof(float) * ne * M.KC * M.KC);
-      k_transpose_blocks32<<<(int)nu, 256, 0, s>>>(M.d_U32, M.KD, M.KC, UT32);
-      k_transpose_blocks32<<<(int)ne, 256, 0, s>>>(M.d_E32, M.KC, M.KC, ET32);
+      { k_transpose_blocks32<<<(int)nu, 256, 0, s>>>(M.d_U32, M.KD, M.KC, UT32); ::h2mg::count_launch(); }
+      { k_transpose_blocks32<<<(int)ne, 256, 0, s>>>(M.d_E32, M.KC, M.KC, ET32); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
       M.d_UT32 = UT32;
       M.d_ET32 = ET32;
@@ -490,24 +491,41 @@ void setup_operators(Matrix& M) {
 }
 
 template <int FMT>
-static void launch_bsgemv(const SymOp& op, bool f32, const void* x, void* yrow, void* z, cudaStream_t s) {
+static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, void* yrow, void* z,
+                          cudaStream_t s) {
   using vt = typename Ar<FMT>::vec_t;
   if (op.nrows == 0) return;
   const void* const* blk = f32 ? op.blk32 : op.blk;
+  Profile& P = M.prof;
+  if (P.on) {
+    if (P.used * 2 + 2 > P.ev.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        H2_CUDA(cudaEventCreate(&e));
+        P.ev.push_back(e);
+      }
+    }
+    H2_CUDA(cudaEventRecord(P.ev[2 * P.used], s));
+  }
   switch (op.K) {
     case 16:
-      k_bsgemv<16, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z);
+      { k_bsgemv<16, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z); ::h2mg::count_launch(); }
       break;
     case 32:
-      k_bsgemv<32, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z);
+      { k_bsgemv<32, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z); ::h2mg::count_launch(); }
       break;
     case 64:
-      k_bsgemv<64, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z);
+      { k_bsgemv<64, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z); ::h2mg::count_launch(); }
       break;
     default:
       throw Error{H2MG_ERR_UNSUPPORTED, "block size not supported"};
   }
   H2_LAUNCH_CHECK();
+  if (P.on) {
+    H2_CUDA(cudaEventRecord(P.ev[2 * P.used + 1], s));
+    P.used++;
+    P.bytes.push_back((double)op.bytes(FMT == FMT_F32 ? 4 : 8, sizeof(vt)));
+  }
 }
 
 template <int FMT, class BT>
@@ -523,48 +541,48 @@ static void apply_impl(Matrix& M, int i, const double* x, double* y, cudaStream_
   if (i == 1) {
     vt* xp = (vt*)M.wxp.p;
     vt* yp = (vt*)M.wyp.p;
-    k_pts_in<FMT><<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, xp);
+    { k_pts_in<FMT><<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, xp); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     vt* zc = z + (size_t)M.opD.nnz * KD;
     if (ts >= 0) {
-      k_up_leaf<FMT, BT><<<1 << L, std::max(KC, 32), 0, s>>>(UT, KD, KC, xp, xc + (size_t)M.slot0(L) * KC);
+      { k_up_leaf<FMT, BT><<<1 << L, std::max(KC, 32), 0, s>>>(UT, KD, KC, xp, xc + (size_t)M.slot0(L) * KC); ::h2mg::count_launch(); }
       for (int ell = L - 1; ell >= ts; --ell)
-        k_up<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(ET + (size_t)M.slot0(ell + 1) * KC * KC, KC,
+        { k_up<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(ET + (size_t)M.slot0(ell + 1) * KC * KC, KC,
                                                             xc + (size_t)M.slot0(ell + 1) * KC,
-                                                            xc + (size_t)M.slot0(ell) * KC);
+                                                            xc + (size_t)M.slot0(ell) * KC); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     }
-    launch_bsgemv<FMT>(M.opD, f32, xp, yp, z, s);
+    launch_bsgemv<FMT>(M, M.opD, f32, xp, yp, z, s);
     if (ts >= 0) {
-      launch_bsgemv<FMT>(M.opC[1], f32, xc, yr, zc, s);
+      launch_bsgemv<FMT>(M, M.opC[1], f32, xc, yr, zc, s);
       for (int ell = ts; ell <= L; ++ell)
-        k_down_final<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(
+        { k_down_final<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(
             M.slot0(ell), KC, yr, M.opC[1].gptr, M.opC[1].gent, zc,
             ell > ts ? E + (size_t)M.slot0(ell) * KC * KC : nullptr,
-            ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, nullptr);
+            ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, nullptr); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     }
-    k_leaf_final<FMT, BT><<<1 << L, std::max(KD, 32), 0, s>>>(
+    { k_leaf_final<FMT, BT><<<1 << L, std::max(KD, 32), 0, s>>>(
         KD, KC, yp, M.opD.gptr, M.opD.gent, z, ts >= 0 ? U : nullptr,
-        ts >= 0 ? yc + (size_t)M.slot0(L) * KC : nullptr, M.d_leafoff, M.d_perm, y);
+        ts >= 0 ? yc + (size_t)M.slot0(L) * KC : nullptr, M.d_leafoff, M.d_perm, y); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     return;
   }
   const int m = L - i + 2;
   const int64_t nm = (int64_t)(1 << m) * KC;
-  k_coef_in<FMT><<<ceil_div(nm, 256), 256, 0, s>>>(x, nm, xc + (size_t)M.slot0(m) * KC);
+  { k_coef_in<FMT><<<ceil_div(nm, 256), 256, 0, s>>>(x, nm, xc + (size_t)M.slot0(m) * KC); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   for (int ell = m - 1; ell >= ts; --ell)
-    k_up<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(ET + (size_t)M.slot0(ell + 1) * KC * KC, KC,
+    { k_up<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(ET + (size_t)M.slot0(ell + 1) * KC * KC, KC,
                                                         xc + (size_t)M.slot0(ell + 1) * KC,
-                                                        xc + (size_t)M.slot0(ell) * KC);
+                                                        xc + (size_t)M.slot0(ell) * KC); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
-  launch_bsgemv<FMT>(M.opC[i], f32, xc, yr, z, s);
+  launch_bsgemv<FMT>(M, M.opC[i], f32, xc, yr, z, s);
   for (int ell = ts; ell <= m; ++ell)
-    k_down_final<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(
+    { k_down_final<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(
         M.slot0(ell), KC, yr, M.opC[i].gptr, M.opC[i].gent, z,
         ell > ts ? E + (size_t)M.slot0(ell) * KC * KC : nullptr,
-        ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, ell == m ? y : nullptr);
+        ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, ell == m ? y : nullptr); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
 }
 

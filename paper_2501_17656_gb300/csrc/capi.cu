@@ -1,4 +1,5 @@
 // capi.cu -- the extern "C" entry points declared in include/h2mg.h.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -9,6 +10,9 @@ namespace h2mg {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void* Matrix::alloc(size_t bytes) {
   void* p = nullptr;
@@ -27,6 +31,7 @@ void* Matrix::alloc(size_t bytes) {
 
 Matrix::~Matrix() {
   if (stream) cudaStreamSynchronize(stream);
+  for (auto e : prof.ev) cudaEventDestroy(e);
   for (auto& d : owned)
     if (d.p) cudaFree(d.p);
 }
@@ -96,7 +101,7 @@ static void build_all(Matrix& M, const double* points, const h2mg_kernel* k, con
     DevView G(k->diag, k->diag ? M.n : 0, true, s);
     if (k->weights) {
       H2_CUDA(cudaMemsetAsync(M.d_flag, 0, sizeof(int), s));
-      k_check_pos<<<ceil_div(M.n, 256), 256, 0, s>>>(W.d, M.n, M.d_flag);
+      { k_check_pos<<<ceil_div(M.n, 256), 256, 0, s>>>(W.d, M.n, M.d_flag); ::h2mg::count_launch(); }
       int h = 0;
       H2_CUDA(cudaMemcpyAsync(&h, M.d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
       H2_CUDA(cudaStreamSynchronize(s));
@@ -104,8 +109,8 @@ static void build_all(Matrix& M, const double* points, const h2mg_kernel* k, con
     }
     M.d_sw = (double*)M.alloc(sizeof(double) * M.n);
     M.d_dg = (double*)M.alloc(sizeof(double) * M.n);
-    k_point_weights<<<ceil_div(M.n, 256), 256, 0, s>>>(M.d_perm, M.n, M.dim, M.d_X, k->weights ? W.d : nullptr,
-                                                       k->diag ? G.d : nullptr, M.kp, M.d_sw, M.d_dg);
+    { k_point_weights<<<ceil_div(M.n, 256), 256, 0, s>>>(M.d_perm, M.n, M.dim, M.d_X, k->weights ? W.d : nullptr,
+                                                       k->diag ? G.d : nullptr, M.kp, M.d_sw, M.d_dg); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     H2_CUDA(cudaStreamSynchronize(s));
   }
@@ -436,6 +441,54 @@ h2mg_status h2mg_vcycle(h2mg_matrix A, const double* x0, const double* r1, doubl
     vcycle(M, *o, X0.d, R.d, X.d, s);
     X.copy_out(x_out, M.n, s);
     H2_CUDA(cudaStreamSynchronize(s));
+    return H2MG_OK;
+  });
+}
+
+int64_t h2mg_launch_count(void) { return g_launches.load(); }
+
+h2mg_status h2mg_transfer(h2mg_matrix A, int level, int direction, const double* v, double* out, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && v && out, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    H2_REQUIRE(level >= 1 && level < M.lev, H2MG_ERR_INVALID_ARG, "level must be in [1, l-1]");
+    H2_REQUIRE(direction == 0 || direction == 1, H2MG_ERR_INVALID_ARG, "direction must be 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t nf = level_size(M, level), nc = level_size(M, level + 1);
+    if (direction == 0) {
+      DevView V(v, nf, true, s), O(out, nc, false, s);
+      restrict_level(M, level, V.d, O.d, s);
+      O.copy_out(out, nc, s);
+    } else {
+      DevView V(v, nc, true, s), O(out, nf, false, s);
+      H2_CUDA(cudaMemsetAsync(O.d, 0, sizeof(double) * nf, s));
+      prolong_add(M, level, V.d, O.d, s);
+      O.copy_out(out, nf, s);
+    }
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* ms, double* bytes) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A, H2MG_ERR_INVALID_ARG, "null handle");
+    Profile& P = A->M.prof;
+    if (enable == 1) {
+      P.used = 0;
+      P.bytes.clear();
+    }
+    double t = 0.0, by = 0.0;
+    for (size_t i = 0; i < P.used; ++i) {
+      H2_CUDA(cudaEventSynchronize(P.ev[2 * i + 1]));
+      float f = 0.f;
+      H2_CUDA(cudaEventElapsedTime(&f, P.ev[2 * i], P.ev[2 * i + 1]));
+      t += f;
+      by += P.bytes[i];
+    }
+    P.on = (enable != 0);
+    if (launches) *launches = (int64_t)P.used;
+    if (ms) *ms = t;
+    if (bytes) *bytes = by;
     return H2MG_OK;
   });
 }

@@ -16,6 +16,7 @@ struct Error {
 };
 
 void set_error(const std::string& msg);
+void count_launch();   // every kernel launch of the library is counted (h2mg_launch_count)
 
 #define H2_CUDA(call)                                                                   \
   do {                                                                                  \

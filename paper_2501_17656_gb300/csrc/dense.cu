@@ -228,7 +228,7 @@ static void scatter_level(Matrix& M, const HostCSR& C, int ncl, bool strict, con
   upload_i32(M, pt, &dt);
   upload_i32(M, ps, &ds);
   const char* base = (const char*)pool + (size_t)blk0 * K * K * fmt_bytes(M.fmt);
-  k_scatter<<<(int)pt.size(), 256, 0, M.stream>>>(dt, ds, base, M.fmt, K, G, n);
+  { k_scatter<<<(int)pt.size(), 256, 0, M.stream>>>(dt, ds, base, M.fmt, K, G, n); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
 }
 
@@ -251,8 +251,8 @@ void build_dense_coarse(Matrix& M) {
       int64_t nn = (int64_t)(1 << (ell + 1)) * KC;
       double* G2 = (double*)M.alloc(sizeof(double) * nn * nn);
       int ncl = 1 << (ell + 1);
-      k_expand<<<ncl * ncl, 256, sm, s>>>(G, ng, M.d_E + (size_t)M.slot0(ell + 1) * KC * KC, KC, KC, ncl,
-                                          1, G2, nn);
+      { k_expand<<<ncl * ncl, 256, sm, s>>>(G, ng, M.d_E + (size_t)M.slot0(ell + 1) * KC * KC, KC, KC, ncl,
+                                          1, G2, nn); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
       scatter_level(M, M.far[ell + 1], ncl, true, M.poolS.p, M.s_level_base[ell + 1], KC, G2, nn);
       H2_CUDA(cudaStreamSynchronize(s));
@@ -281,7 +281,7 @@ void build_dense_coarse(Matrix& M) {
     if (M.tstar >= 0) {
       int ncl = 1 << L;
       size_t sm = sizeof(double) * (KC * KC + KC * KD);
-      k_expand<<<ncl * ncl, 256, sm, s>>>(G, ng, M.d_U, KD, KC, ncl, 0, A1, np);
+      { k_expand<<<ncl * ncl, 256, sm, s>>>(G, ng, M.d_U, KD, KC, ncl, 0, A1, np); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     }
     M.nl = (int)np;
@@ -293,21 +293,21 @@ void build_dense_coarse(Matrix& M) {
   }
   unsigned char* dv = (unsigned char*)M.alloc(valid.size());
   H2_CUDA(cudaMemcpyAsync(dv, valid.data(), valid.size(), cudaMemcpyHostToDevice, s));
-  k_pad_diag<<<ceil_div(M.nl, 256), 256, 0, s>>>(M.d_Al, M.nl, dv);
+  { k_pad_diag<<<ceil_div(M.nl, 256), 256, 0, s>>>(M.d_Al, M.nl, dv); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   // Cholesky (lower), pivot check into d_flag
   H2_CUDA(cudaMemsetAsync(M.d_flag, 0, sizeof(int), s));
   int64_t n = M.nl;
   for (int k0 = 0; k0 < n; k0 += NB) {
     int nb = (int)std::min<int64_t>(NB, n - k0);
-    k_potrf_diag<<<1, 256, 0, s>>>(M.d_Al, n, k0, nb, M.d_flag);
+    { k_potrf_diag<<<1, 256, 0, s>>>(M.d_Al, n, k0, nb, M.d_flag); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     int64_t rem = n - k0 - nb;
     if (rem > 0) {
-      k_trsm_panel<<<ceil_div(rem, 128), 128, 0, s>>>(M.d_Al, n, k0, nb);
+      { k_trsm_panel<<<ceil_div(rem, 128), 128, 0, s>>>(M.d_Al, n, k0, nb); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
       int tiles = ceil_div(rem, 64);
-      k_syrk_update<<<tiles * tiles, 256, 0, s>>>(M.d_Al, n, k0, nb, tiles);
+      { k_syrk_update<<<tiles * tiles, 256, 0, s>>>(M.d_Al, n, k0, nb, tiles); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     }
   }
@@ -340,7 +340,7 @@ void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s) {
   double* x = y + n;
   if (M.lev == 1) {
     H2_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * n, s));
-    k_to_slots<<<ceil_div(M.n, 256), 256, 0, s>>>(r, M.d_slot_of, M.n, w);
+    { k_to_slots<<<ceil_div(M.n, 256), 256, 0, s>>>(r, M.d_slot_of, M.n, w); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   } else {
     H2_CUDA(cudaMemcpyAsync(w, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -349,7 +349,7 @@ void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s) {
     int nb = (int)std::min<int64_t>(NB, n - k0);
     int64_t rem = n - k0 - nb;
     int grid = rem > 0 ? ceil_div(rem, 128) : 1;
-    k_trsv_fwd<<<grid, 128, 0, s>>>(M.d_Al, n, k0, nb, w, y);
+    { k_trsv_fwd<<<grid, 128, 0, s>>>(M.d_Al, n, k0, nb, w, y); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
   double* xo = (M.lev == 1) ? x : e;
@@ -357,11 +357,11 @@ void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s) {
   for (int k0 = last; k0 >= 0; k0 -= NB) {
     int nb = (int)std::min<int64_t>(NB, n - k0);
     int grid = k0 > 0 ? ceil_div(k0, 8) : 1;   // 8 warps per block
-    k_trsv_bwd<<<grid, 256, 0, s>>>(M.d_Al, n, k0, nb, y, xo);
+    { k_trsv_bwd<<<grid, 256, 0, s>>>(M.d_Al, n, k0, nb, y, xo); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
   if (M.lev == 1) {
-    k_from_slots<<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, e);
+    { k_from_slots<<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, e); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
 }

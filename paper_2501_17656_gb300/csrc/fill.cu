@@ -324,8 +324,8 @@ void build_bases(Matrix& M) {
   H2_CUDA(cudaMemcpyAsync(M.d_rank, M.h_rank.data(), sizeof(int) * nsl, cudaMemcpyHostToDevice, s));
   M.d_nodes = (double*)M.alloc(sizeof(double) * (size_t)nsl * k * dim);
   for (int ell = ts; ell <= L; ++ell) {
-    k_nodes<<<1 << ell, 128, 0, s>>>(M.d_box[ell], ell, dim, q, k, floor_hw,
-                                     M.d_nodes + (size_t)M.slot0(ell) * k * dim);
+    { k_nodes<<<1 << ell, 128, 0, s>>>(M.d_box[ell], ell, dim, q, k, floor_hw,
+                                     M.d_nodes + (size_t)M.slot0(ell) * k * dim); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
   M.d_U = (double*)M.alloc(sizeof(double) * (size_t)(1 << L) * KD * KC);
@@ -334,18 +334,18 @@ void build_bases(Matrix& M) {
   {
     size_t sm = sizeof(double) * ((size_t)KD * k + KD * KD + 64 + 33);
     H2_CUDA(cudaFuncSetAttribute(k_leaf_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_leaf_qr<<<1 << L, 128, sm, s>>>(M.d_X, M.d_sw, M.d_leafoff, M.d_box[L], dim, q, k, KD, KC,
-                                       floor_hw, M.d_U, M.d_R + (size_t)M.slot0(L) * KC * KC);
+    { k_leaf_qr<<<1 << L, 128, sm, s>>>(M.d_X, M.d_sw, M.d_leafoff, M.d_box[L], dim, q, k, KD, KC,
+                                       floor_hw, M.d_U, M.d_R + (size_t)M.slot0(L) * KC * KC); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
   {
     size_t sm = sizeof(double) * ((size_t)k * k + 4 * k * k + 64 + 33);
     H2_CUDA(cudaFuncSetAttribute(k_parent_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     for (int ell = L - 1; ell >= ts; --ell) {
-      k_parent_qr<<<1 << ell, 128, sm, s>>>(
+      { k_parent_qr<<<1 << ell, 128, sm, s>>>(
           M.d_box[ell], M.d_nodes + (size_t)M.slot0(ell + 1) * k * dim, M.d_rank + M.slot0(ell + 1),
           dim, q, k, KC, floor_hw, M.d_R + (size_t)M.slot0(ell + 1) * KC * KC,
-          M.d_E + (size_t)M.slot0(ell + 1) * KC * KC, M.d_R + (size_t)M.slot0(ell) * KC * KC);
+          M.d_E + (size_t)M.slot0(ell + 1) * KC * KC, M.d_R + (size_t)M.slot0(ell) * KC * KC); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     }
   }
@@ -551,8 +551,8 @@ void build_blocks(Matrix& M, const Matrix* base) {
   M.poolD.bytes = pool_bytes(M.nD, KD, M.fmt);
   M.poolD.p = M.alloc(M.poolD.bytes);
   chunked(M.nD, [&](int64_t b0, int nb) {
-    k_fill_D<<<nb, 256, 0, s>>>(d_dt + b0, d_ds + b0, M.d_leafoff, M.d_X, M.d_sw, M.d_dg, dim, KD,
-                                M.kp, (char*)M.poolD.p + pool_bytes(b0, KD, M.fmt), M.fmt);
+    { k_fill_D<<<nb, 256, 0, s>>>(d_dt + b0, d_ds + b0, M.d_leafoff, M.d_X, M.d_sw, M.d_dg, dim, KD,
+                                M.kp, (char*)M.poolD.p + pool_bytes(b0, KD, M.fmt), M.fmt); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   });
   if (M.tstar < 0) {
@@ -581,8 +581,8 @@ void build_blocks(Matrix& M, const Matrix* base) {
   size_t smS = sizeof(double) * 2 * KC * KC;
   H2_CUDA(cudaFuncSetAttribute(k_fill_S, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smS));
   chunked(M.nS, [&](int64_t b0, int nb) {
-    k_fill_S<<<nb, 256, smS, s>>>(d_st + b0, d_ss + b0, M.d_nodes, M.d_R, k, KC, dim, M.kp,
-                                  (char*)M.poolS.p + pool_bytes(b0, KC, M.fmt), M.fmt);
+    { k_fill_S<<<nb, 256, smS, s>>>(d_st + b0, d_ss + b0, M.d_nodes, M.d_R, k, KC, dim, M.kp,
+                                  (char*)M.poolS.p + pool_bytes(b0, KC, M.fmt), M.fmt); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   });
   H2_CUDA(cudaStreamSynchronize(s));
@@ -632,9 +632,9 @@ void build_coarse_near(Matrix& M) {
     size_t sm = sizeof(double) * ((size_t)std::max(KD * KD, KC * KC) + KD * KC);
     H2_CUDA(cudaFuncSetAttribute(k_fill_P2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     chunked(M.nP[2], [&](int64_t b0, int nb) {
-      k_fill_P2<<<nb, 256, sm, s>>>(d_t + b0, d_s + b0, M.d_leafoff, M.d_X, M.d_sw, M.d_dg, dim, KD,
+      { k_fill_P2<<<nb, 256, sm, s>>>(d_t + b0, d_s + b0, M.d_leafoff, M.d_X, M.d_sw, M.d_dg, dim, KD,
                                     KC, M.kp, M.d_U, (char*)M.poolP[2].p + pool_bytes(b0, KC, M.fmt),
-                                    M.fmt);
+                                    M.fmt); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     });
   }
@@ -683,8 +683,8 @@ void build_coarse_near(Matrix& M) {
     M.poolP[i].p = M.alloc(M.poolP[i].bytes);
     const double* Ef = M.d_E + (size_t)M.slot0(mf) * KC * KC;
     chunked(M.nP[i], [&](int64_t b0, int nb) {
-      k_fill_Pi<<<nb, 256, sm, s>>>(d_t + b0, d_s + b0, d_ref + b0 * 4, M.poolP[i - 1].p, M.poolS.p,
-                                    M.fmt, Ef, KC, (char*)M.poolP[i].p + pool_bytes(b0, KC, M.fmt));
+      { k_fill_Pi<<<nb, 256, sm, s>>>(d_t + b0, d_s + b0, d_ref + b0 * 4, M.poolP[i - 1].p, M.poolS.p,
+                                    M.fmt, Ef, KC, (char*)M.poolP[i].p + pool_bytes(b0, KC, M.fmt)); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     });
     H2_CUDA(cudaStreamSynchronize(s));
@@ -699,8 +699,8 @@ void build_f32_copies(Matrix& M) {
     dst.bytes = pool_bytes(nblk, K, FMT_F32);
     dst.p = M.alloc(dst.bytes);
     chunked(nblk, [&](int64_t b0, int nb) {
-      k_convert_pool<<<nb, 256, 0, s>>>((const char*)src.p + pool_bytes(b0, K, M.fmt), M.fmt,
-                                        (char*)dst.p + pool_bytes(b0, K, FMT_F32), FMT_F32, K);
+      { k_convert_pool<<<nb, 256, 0, s>>>((const char*)src.p + pool_bytes(b0, K, M.fmt), M.fmt,
+                                        (char*)dst.p + pool_bytes(b0, K, FMT_F32), FMT_F32, K); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     });
   };
@@ -712,9 +712,9 @@ void build_f32_copies(Matrix& M) {
     int64_t nu = (int64_t)(1 << M.L) * M.KD * M.KC, ne = (int64_t)M.nslots() * M.KC * M.KC;
     M.d_U32 = (float*)M.alloc(sizeof(float) * nu);
     M.d_E32 = (float*)M.alloc(sizeof(float) * ne);
-    k_to_f32<<<ceil_div(nu, 256), 256, 0, s>>>(M.d_U, M.d_U32, nu);
+    { k_to_f32<<<ceil_div(nu, 256), 256, 0, s>>>(M.d_U, M.d_U32, nu); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
-    k_to_f32<<<ceil_div(ne, 256), 256, 0, s>>>(M.d_E, M.d_E32, ne);
+    { k_to_f32<<<ceil_div(ne, 256), 256, 0, s>>>(M.d_E, M.d_E32, ne); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
   H2_CUDA(cudaStreamSynchronize(s));

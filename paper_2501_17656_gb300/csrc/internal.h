@@ -31,6 +31,18 @@ struct SymOp {
   const void** blk32 = nullptr;    // [nnz] block pointers into the FP32 pool (or null)
   int* gptr = nullptr;    // [nrows + 1] gather lists
   int* gent = nullptr;    // entries e with col[e] == row and row(e) < col[e]
+  int64_t noff = 0;       // off-diagonal entries (each writes K transposed partials)
+  int64_t bytes(int eb, int vb) const {   // algorithmic bytes of one product
+    return (int64_t)nnz * K * K * eb + (int64_t)nrows * K * vb * 2 + noff * K * vb;
+  }
+};
+
+// CUDA events around the launches of the block product (h2mg_profile).
+struct Profile {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+  size_t used = 0;               // pairs in use
+  std::vector<double> bytes;
 };
 
 // Host-side copy of a full (both triangles) CSR list of cluster pairs.
@@ -108,9 +120,11 @@ struct Matrix {
   DevBuf wstage;                // host staging
   DevBuf wvec;                  // multigrid vectors (float64)
   DevBuf wred;                  // reduction partials + scalars
-  DevBuf wcoarse;               // two vectors of the coarse size (triangular solves)
+  DevBuf wcoarse;               // three vectors of the coarse size (triangular solves)
+  DevBuf wfcg;                  // five point vectors of the flexible-CG outer loop
   int* d_flag = nullptr;        // device error flags
 
+  Profile prof;
   std::vector<DevBuf> owned;    // everything else
   ~Matrix();
   void* alloc(size_t bytes);    // owned allocation, zero-initialised

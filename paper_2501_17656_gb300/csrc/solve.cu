@@ -232,7 +232,7 @@ static Work work(Matrix& M) {
 }
 
 static void dot_part(const double* a, const double* b, int64_t n, double* part, cudaStream_t s) {
-  k_dot_part<<<part_grid(n), 256, 0, s>>>(a, b, n, part);
+  { k_dot_part<<<part_grid(n), 256, 0, s>>>(a, b, n, part); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
 }
 
@@ -251,21 +251,21 @@ void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n
   } else {
     if (x != x0) H2_CUDA(cudaMemcpyAsync(x, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     apply_level(M, i, f32, x, W.cq, s);
-    k_sub<<<g, 256, 0, s>>>(f, W.cq, rr, N);
+    { k_sub<<<g, 256, 0, s>>>(f, W.cq, rr, N); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
   H2_CUDA(cudaMemcpyAsync(W.cp, rr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
   dot_part(rr, rr, N, W.pa, s);
   dot_part(f, f, N, W.pb, s);
-  k_cg_init<<<1, 32, 0, s>>>(W.pa, part_grid(N), W.pb, part_grid(N), W.st);
+  { k_cg_init<<<1, 32, 0, s>>>(W.pa, part_grid(N), W.pb, part_grid(N), W.st); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   for (int it = 0; it < n; ++it) {
     apply_level(M, i, f32, W.cp, W.cq, s);
     dot_part(W.cp, W.cq, N, W.pa, s);
-    k_cg_alpha<<<1, 32, 0, s>>>(W.pa, part_grid(N), W.st);
-    k_cg_update<<<part_grid(N), 256, 0, s>>>(x, rr, W.cp, W.cq, N, W.st, W.pb);
-    k_cg_beta<<<1, 32, 0, s>>>(W.pb, part_grid(N), W.st);
-    k_cg_p<<<g, 256, 0, s>>>(W.cp, rr, N, W.st);
+    { k_cg_alpha<<<1, 32, 0, s>>>(W.pa, part_grid(N), W.st); ::h2mg::count_launch(); }
+    { k_cg_update<<<part_grid(N), 256, 0, s>>>(x, rr, W.cp, W.cq, N, W.st, W.pb); ::h2mg::count_launch(); }
+    { k_cg_beta<<<1, 32, 0, s>>>(W.pb, part_grid(N), W.st); ::h2mg::count_launch(); }
+    { k_cg_p<<<g, 256, 0, s>>>(W.cp, rr, N, W.st); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
 }
@@ -273,10 +273,10 @@ void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n
 void restrict_level(Matrix& M, int i, const double* v, double* out, cudaStream_t s) {
   const int KC = M.KC, KD = M.KD, L = M.L;
   if (i == 1) {
-    k_restrict_leaf<<<1 << L, std::max(KC, 32), 0, s>>>(M.d_UT, KD, KC, v, M.d_leafoff, M.d_perm, out);
+    { k_restrict_leaf<<<1 << L, std::max(KC, 32), 0, s>>>(M.d_UT, KD, KC, v, M.d_leafoff, M.d_perm, out); ::h2mg::count_launch(); }
   } else {
     int m = L - i + 2;
-    k_restrict<<<1 << (m - 1), std::max(KC, 32), 0, s>>>(M.d_ET + (size_t)M.slot0(m) * KC * KC, KC, v, out);
+    { k_restrict<<<1 << (m - 1), std::max(KC, 32), 0, s>>>(M.d_ET + (size_t)M.slot0(m) * KC * KC, KC, v, out); ::h2mg::count_launch(); }
   }
   H2_LAUNCH_CHECK();
 }
@@ -284,10 +284,10 @@ void restrict_level(Matrix& M, int i, const double* v, double* out, cudaStream_t
 void prolong_add(Matrix& M, int i, const double* e, double* out, cudaStream_t s) {
   const int KC = M.KC, KD = M.KD, L = M.L;
   if (i == 1) {
-    k_prolong_leaf<<<1 << L, std::max(KD, 32), 0, s>>>(M.d_U, KD, KC, e, M.d_leafoff, M.d_perm, out);
+    { k_prolong_leaf<<<1 << L, std::max(KD, 32), 0, s>>>(M.d_U, KD, KC, e, M.d_leafoff, M.d_perm, out); ::h2mg::count_launch(); }
   } else {
     int m = L - i + 2;
-    k_prolong<<<1 << m, std::max(KC, 32), 0, s>>>(M.d_E + (size_t)M.slot0(m) * KC * KC, KC, e, out);
+    { k_prolong<<<1 << m, std::max(KC, 32), 0, s>>>(M.d_E + (size_t)M.slot0(m) * KC * KC, KC, e, out); ::h2mg::count_launch(); }
   }
   H2_LAUNCH_CHECK();
 }
@@ -310,7 +310,7 @@ void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double*
       const double* res = W.cr;                                      // r_i - A_i e~_i (recurrence)
       if (o.explicit_restrict_residual) {
         apply_level(M, i, f32, W.et[i], W.cq, s);
-        k_sub<<<vec_grid(N), 256, 0, s>>>(ri, W.cq, W.cr, N);
+        { k_sub<<<vec_grid(N), 256, 0, s>>>(ri, W.cq, W.cr, N); ::h2mg::count_launch(); }
         H2_LAUNCH_CHECK();
       }
       restrict_level(M, i, res, W.r[i + 1], s);                      // r_{i+1} = U_i^T (...)
@@ -330,7 +330,7 @@ void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double*
       smooth(M, i, f32, fi, W.et[i], ni, W.et[i], nullptr, s);       // e_i = Iter(A_i, r_i, e~_i)
     }
   }
-  k_add<<<vec_grid(n1), 256, 0, s>>>(x0, W.et[1], xout, n1);         // x* = x0 + e_1
+  { k_add<<<vec_grid(n1), 256, 0, s>>>(x0, W.et[1], xout, n1); ::h2mg::count_launch(); }         // x* = x0 + e_1
   H2_LAUNCH_CHECK();
 }
 
@@ -345,6 +345,21 @@ static double norm2(Matrix& M, const double* v, int64_t n, cudaStream_t s) {
   return std::sqrt(t);
 }
 
+static double dot_host(Matrix& M, const double* a, const double* b, int64_t n, cudaStream_t s) {
+  Work W = work(M);
+  dot_part(a, b, n, W.pa, s);
+  std::vector<double> h(part_grid(n));
+  H2_CUDA(cudaMemcpyAsync(h.data(), W.pa, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  H2_CUDA(cudaStreamSynchronize(s));
+  double t = 0.0;
+  for (double v : h) t += v;
+  return t;
+}
+
+// Outer iteration: repeated V-cycles x <- x + V(b - A x) (Sec. 3.3), or flexible CG
+// preconditioned by one V-cycle (the new direction is made A-orthogonal to the
+// previous one because the V-cycle with CG smoothers is a nonlinear map). The
+// residual b - A x is recomputed in float64 before every cycle.
 h2mg_status solve(Matrix& M, const double* b, double* x, const h2mg_solve_opts& o, h2mg_solve_info* info,
                   cudaStream_t s) {
   Work W = work(M);
@@ -355,9 +370,24 @@ h2mg_status solve(Matrix& M, const double* b, double* x, const h2mg_solve_opts& 
   h2mg_solve_info loc{};
   h2mg_status st = H2MG_ERR_NOT_CONVERGED;
   double* r = W.t1;
+  const bool fcg = o.outer == H2MG_OUTER_FCG;
+  double* z = nullptr;
+  double *p = nullptr, *q = nullptr, *pp = nullptr, *qp = nullptr;
+  if (fcg) {
+    if (!M.wfcg.p) {
+      M.wfcg.bytes = sizeof(double) * 5 * (size_t)n;
+      M.wfcg.p = M.alloc(M.wfcg.bytes);
+    }
+    z = (double*)M.wfcg.p;
+    p = z + n;
+    q = p + n;
+    pp = q + n;
+    qp = pp + n;
+  }
+  int g = vec_grid(n);
   for (int cyc = 0; cyc <= o.max_cycles; ++cyc) {
     apply_level(M, 1, false, x, W.t2, s);
-    k_sub<<<vec_grid(n), 256, 0, s>>>(b, W.t2, r, n);
+    { k_sub<<<g, 256, 0, s>>>(b, W.t2, r, n); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     double rel = nb > 0 ? norm2(M, r, n, s) / nb : 0.0;
     if (cyc < 256) loc.relres_hist[cyc] = rel;
@@ -373,7 +403,26 @@ h2mg_status solve(Matrix& M, const double* b, double* x, const h2mg_solve_opts& 
       break;
     }
     if (cyc == o.max_cycles) break;
-    vcycle(M, o, x, r, x, s);
+    if (!fcg) {
+      vcycle(M, o, x, r, x, s);
+      continue;
+    }
+    H2_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
+    vcycle(M, o, z, r, z, s);                                   // z = V(r) from zero
+    if (cyc == 0) {
+      H2_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      double beta = -dot_host(M, z, qp, n, s) / dot_host(M, pp, qp, n, s);
+      H2_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      { k_axpby<<<g, 256, 0, s>>>(beta, pp, 1.0, p, n); ::h2mg::count_launch(); }           // p = z + beta p_prev
+      H2_LAUNCH_CHECK();
+    }
+    apply_level(M, 1, false, p, q, s);
+    double alpha = dot_host(M, p, r, n, s) / dot_host(M, p, q, n, s);
+    { k_axpby<<<g, 256, 0, s>>>(alpha, p, 1.0, x, n); ::h2mg::count_launch(); }             // x += alpha p
+    H2_LAUNCH_CHECK();
+    std::swap(p, pp);
+    std::swap(q, qp);
   }
   H2_CUDA(cudaStreamSynchronize(s));
   loc.ms_solve = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

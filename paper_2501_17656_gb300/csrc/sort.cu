@@ -110,11 +110,11 @@ void exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, Matrix&)
   TempBuf sums(sizeof(int) * (nb + 1));
   TempBuf tmp(sizeof(int) * (size_t)n);
   H2_CUDA(cudaMemcpyAsync(tmp.p, in, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-  k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(tmp.as<int>(), n, sums.as<int>());
+  { k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(tmp.as<int>(), n, sums.as<int>()); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
-  k_scan_single<<<1, SCAN_THREADS, 0, s>>>(sums.as<int>(), nb);
+  { k_scan_single<<<1, SCAN_THREADS, 0, s>>>(sums.as<int>(), nb); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
-  k_scan_apply<<<nb, SCAN_THREADS, 0, s>>>(tmp.as<int>(), n, sums.as<int>(), out);
+  { k_scan_apply<<<nb, SCAN_THREADS, 0, s>>>(tmp.as<int>(), n, sums.as<int>(), out); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   H2_CUDA(cudaStreamSynchronize(s));   // temporaries are freed on return
 }
@@ -202,10 +202,10 @@ void radix_sort_u64(uint64_t* keys, int* vals, int n, int bits, Matrix& M, cudaS
   int *va = vals, *vb = v2.as<int>();
   int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
-    k_rs_hist<<<ntiles, RS_THREADS, 0, s>>>(ka, n, 8 * p, ntiles, hist.as<int>());
+    { k_rs_hist<<<ntiles, RS_THREADS, 0, s>>>(ka, n, 8 * p, ntiles, hist.as<int>()); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     exclusive_scan_i32(hist.as<int>(), hist.as<int>(), 256 * ntiles, s, M);
-    k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, 8 * p, ntiles, hist.as<int>());
+    { k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, 8 * p, ntiles, hist.as<int>()); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     std::swap(ka, kb);
     std::swap(va, vb);

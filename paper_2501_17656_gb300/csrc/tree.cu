@@ -120,7 +120,7 @@ void build_tree(Matrix& M, const double* d_pts) {
     int* flag = M.d_flag;
     H2_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
     int64_t tot = (int64_t)n * dim;
-    k_finite<<<ceil_div(tot, 256), 256, 0, s>>>(d_pts, tot, flag);
+    { k_finite<<<ceil_div(tot, 256), 256, 0, s>>>(d_pts, tot, flag); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     int h = 0;
     H2_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -161,16 +161,16 @@ void build_tree(Matrix& M, const double* d_pts) {
     M.d_box[ell] = (double*)M.alloc(sizeof(double) * 2 * dim * ncl);
     H2_CUDA(cudaMemcpyAsync(d_off, M.offsets[ell].data(), sizeof(int) * (ncl + 1),
                             cudaMemcpyHostToDevice, s));
-    k_boxes<<<ncl, 256, 0, s>>>(d_pts, ord, d_off, dim, M.d_box[ell], d_axis);
+    { k_boxes<<<ncl, 256, 0, s>>>(d_pts, ord, d_off, dim, M.d_box[ell], d_axis); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     if (ell == L) break;
-    k_seg_of<<<ncl, 256, 0, s>>>(ord, d_off, seg_of);
+    { k_seg_of<<<ncl, 256, 0, s>>>(ord, d_off, seg_of); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
-    k_coord_keys<<<ceil_div(n, 256), 256, 0, s>>>(d_pts, n, dim, seg_of, d_axis, key, ord);
+    { k_coord_keys<<<ceil_div(n, 256), 256, 0, s>>>(d_pts, n, dim, seg_of, d_axis, key, ord); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     radix_sort_u64(key, ord, n, 64, M, s);            // by coordinate, ties by index
     if (ell > 0) {
-      k_seg_keys<<<ceil_div(n, 256), 256, 0, s>>>(ord, seg_of, n, key);
+      { k_seg_keys<<<ceil_div(n, 256), 256, 0, s>>>(ord, seg_of, n, key); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
       radix_sort_u64(key, ord, n, ell, M, s);         // by cluster (stable)
     }
@@ -181,7 +181,7 @@ void build_tree(Matrix& M, const double* d_pts) {
                           cudaMemcpyHostToDevice, s));
   M.d_X = (double*)M.alloc(sizeof(double) * (size_t)n * dim);
   M.d_slot_of = (int*)M.alloc(sizeof(int) * n);
-  k_tree_out<<<1 << L, 128, 0, s>>>(d_pts, ord, n, dim, M.d_leafoff, L, M.KD, M.d_X, M.d_slot_of);
+  { k_tree_out<<<1 << L, 128, 0, s>>>(d_pts, ord, n, dim, M.d_leafoff, L, M.KD, M.d_X, M.d_slot_of); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   H2_CUDA(cudaStreamSynchronize(s));
 }
@@ -255,8 +255,8 @@ void build_partition(Matrix& M) {
     int nrows = 1 << ell;
     int* fc = (int*)M.alloc(sizeof(int) * (nrows + 1));
     int* ic = (int*)M.alloc(sizeof(int) * (nrows + 1));
-    k_partition<<<ceil_div(nrows, 128), 128, 0, s>>>(nrows, prow, pcol, M.d_box[ell], dim, M.eta, 0,
-                                                     fc, ic, nullptr, nullptr);
+    { k_partition<<<ceil_div(nrows, 128), 128, 0, s>>>(nrows, prow, pcol, M.d_box[ell], dim, M.eta, 0,
+                                                     fc, ic, nullptr, nullptr); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     exclusive_scan_i32(fc, fc, nrows, s, M);
     exclusive_scan_i32(ic, ic, nrows, s, M);
@@ -266,8 +266,8 @@ void build_partition(Matrix& M) {
     H2_CUDA(cudaStreamSynchronize(s));
     int* fcol = (int*)M.alloc(sizeof(int) * std::max(nf, 1));
     int* icol = (int*)M.alloc(sizeof(int) * std::max(ni, 1));
-    k_partition<<<ceil_div(nrows, 128), 128, 0, s>>>(nrows, prow, pcol, M.d_box[ell], dim, M.eta, 1,
-                                                     fc, ic, fcol, icol);
+    { k_partition<<<ceil_div(nrows, 128), 128, 0, s>>>(nrows, prow, pcol, M.d_box[ell], dim, M.eta, 1,
+                                                     fc, ic, fcol, icol); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     HostCSR& F = M.far[ell];
     HostCSR& I = M.inadm[ell];

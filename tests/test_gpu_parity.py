@@ -142,6 +142,13 @@ def test_coarse_solve_matches_oracle(pair):
         assert rel(e, mg.dir_sol(r)) < 1e-10
         return
     KC = A.query("KC")
+    if mg.chol is None:
+        # the interpolation error exceeds the smallest eigenvalue: both sides must
+        # find the coarse operator indefinite
+        with pytest.raises(pkg.H2MGError) as err:
+            A.coarse_solve(cuda(_pad(mg, l, r, KC)))
+        assert err.value.name == "NOT_SPD"
+        return
     e = A.coarse_solve(cuda(_pad(mg, l, r, KC))).cpu().numpy()
     ref = mg.dir_sol(r)
     kappa = np.linalg.cond(mg.Al)
@@ -172,6 +179,8 @@ def test_vcycle_matches_oracle_short_smoothing(pair):
     GPU and the oracle agree to rounding."""
     name, X, A, h = pair
     mg = H2MG(h)
+    if mg.chol is None:
+        pytest.skip("indefinite H2 approximation")
     from oracle.mg import vcycle
     b = np.random.default_rng(16).standard_normal(X.shape[0])
     o = SolveOpts(n_f=1, n_c=2)
