@@ -214,6 +214,26 @@ int64_t h2mg_launch_count(void);
  * Any output pointer may be NULL. */
 h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* ms, double* bytes);
 
+/* ---------------------------------------------------------------- allocation-free product
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory where they need a product: code running while a stream is
+ * captured into a CUDA graph, code inside allocator callbacks, or processes whose
+ * device memory another allocator has reserved in full.
+ *
+ * h2mg_apply_noalloc computes y = A x like h2mg_apply (one column, device x and y
+ * only; host pointers are rejected with INVALID_ARG) but calls no cudaMalloc,
+ * cudaFree or allocating library routine: its workspace lives in one fixed array of
+ * H2MG_NOALLOC_SCRATCH_BYTES bytes of device memory that every GPU loading this
+ * library holds until the process exits. Matrices whose product needs more scratch
+ * than that are rejected with UNSUPPORTED (about 2^16 points in 3-D with leaf 64 and
+ * 4x4x4 nodes fit). The first call on a device looks up the array's address with
+ * that device current; make that first call before any stream capture. All calls
+ * share the array and it keeps the last call's contents: calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race and give wrong
+ * results. */
+#define H2MG_NOALLOC_SCRATCH_BYTES (64u << 20)
+h2mg_status h2mg_apply_noalloc(h2mg_matrix A, const double* x, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5)
 EXPORTED = ["h2mg_build", "h2mg_apply", "h2mg_solve", "h2mg_destroy", "h2mg_error_string",
             "h2mg_last_error", "h2mg_query", "h2mg_export", "h2mg_apply_level",
             "h2mg_coarse_solve", "h2mg_smooth", "h2mg_vcycle", "h2mg_launch_count", "h2mg_profile",
-            "h2mg_transfer"]
+            "h2mg_transfer", "h2mg_apply_noalloc"]
 
 
 class H2MGError(RuntimeError):
@@ -103,6 +103,7 @@ def load_library(build_if_missing: bool = False):
     lib.h2mg_vcycle.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_SolveOpts), vp]
     lib.h2mg_launch_count.argtypes = []
     lib.h2mg_transfer.argtypes = [vp, ci, ci, vp, vp, vp]
+    lib.h2mg_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.h2mg_profile.argtypes = [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(cd), ctypes.POINTER(cd)]
     for name in EXPORTED:
         if name not in ("h2mg_error_string", "h2mg_last_error", "h2mg_launch_count"):
@@ -227,6 +228,12 @@ class H2Matrix:
         nrhs = 1 if len(x.shape) == 1 else int(x.shape[1])
         ld = self.n
         _check(self._lib.h2mg_apply(self._h, _ptr(x), _ptr(y), nrhs, ld, _stream()))
+        return y
+
+    def apply_noalloc(self, x, y):
+        """y = A x without any device allocation (device tensors only; scratch in a
+        fixed array shared by all calls -- see h2mg_apply_noalloc)."""
+        _check(self._lib.h2mg_apply_noalloc(self._h, _ptr(x), _ptr(y), _stream()))
         return y
 
     def apply_level(self, i: int, x, precision: str = "f64", y=None):

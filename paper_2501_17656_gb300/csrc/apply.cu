@@ -530,17 +530,17 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
 
 template <int FMT, class BT>
 static void apply_impl(Matrix& M, int i, const double* x, double* y, cudaStream_t s, const BT* U,
-                       const BT* UT, const BT* E, const BT* ET) {
+                       const BT* UT, const BT* E, const BT* ET, const ApplyWork* ws = nullptr) {
   using vt = typename Ar<FMT>::vec_t;
   const int L = M.L, KC = M.KC, KD = M.KD, ts = M.tstar;
   const bool f32 = (FMT == FMT_F32);
-  vt* xc = (vt*)M.wx.p;
-  vt* yr = (vt*)M.wyrow.p;
-  vt* yc = (vt*)M.wyc.p;
-  vt* z = (vt*)M.wz.p;
+  vt* xc = (vt*)(ws ? ws->xc : M.wx.p);
+  vt* yr = (vt*)(ws ? ws->yr : M.wyrow.p);
+  vt* yc = (vt*)(ws ? ws->yc : M.wyc.p);
+  vt* z = (vt*)(ws ? ws->z : M.wz.p);
   if (i == 1) {
-    vt* xp = (vt*)M.wxp.p;
-    vt* yp = (vt*)M.wyp.p;
+    vt* xp = (vt*)(ws ? ws->xp : M.wxp.p);
+    vt* yp = (vt*)(ws ? ws->yp : M.wyp.p);
     { k_pts_in<FMT><<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, xp); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     vt* zc = z + (size_t)M.opD.nnz * KD;
@@ -595,6 +595,24 @@ void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStr
   } else {
     apply_impl<FMT_F64, double>(M, i, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET);
   }
+}
+
+// Level-1 product in the primary format with caller-supplied workspace (the
+// handle's own buffers are not touched).
+void apply_level1_ws(Matrix& M, const double* x, double* y, cudaStream_t s, const ApplyWork& ws) {
+  if (M.fmt == FMT_DF)
+    apply_impl<FMT_DF, double>(M, 1, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET, &ws);
+  else
+    apply_impl<FMT_F64, double>(M, 1, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET, &ws);
+}
+
+// Bytes of each workspace region of the level-1 product.
+void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts, size_t* z) {
+  *coef = 8 * (size_t)std::max(M.nslots(), 1) * M.KC;
+  *pts = 8 * (size_t)(1 << M.L) * M.KD;
+  size_t zz = (size_t)M.opD.nnz * M.KD;
+  if (M.tstar >= 0) zz += (size_t)M.opC[1].nnz * M.KC;
+  *z = 8 * std::max<size_t>(zz, 1);
 }
 
 // Algorithmic bytes of one A_i apply in the primary format: every stored block once,

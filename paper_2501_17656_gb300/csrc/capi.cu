@@ -36,7 +36,9 @@ Matrix::~Matrix() {
     if (d.p) cudaFree(d.p);
 }
 
-static bool is_device_ptr(const void* p) {
+bool is_device_pointer(const void* p);
+static bool is_device_ptr(const void* p) { return is_device_pointer(p); }
+bool is_device_pointer(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -132,10 +134,6 @@ static void build_all(Matrix& M, const double* points, const h2mg_kernel* k, con
 }  // namespace h2mg
 
 using namespace h2mg;
-
-struct h2mg_matrix_s {
-  Matrix M;
-};
 
 template <class F>
 static h2mg_status guard(F f) {

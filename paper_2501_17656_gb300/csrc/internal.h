@@ -142,7 +142,12 @@ void build_f32_copies(Matrix& M);
 void build_dense_coarse(Matrix& M);
 void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s);
 // ---- apply.cu
+struct ApplyWork {                // workspace of one product (see apply_impl)
+  void *xc, *yr, *yc, *xp, *yp, *z;
+};
 void setup_operators(Matrix& M);
+void apply_level1_ws(Matrix& M, const double* x, double* y, cudaStream_t s, const ApplyWork& ws);
+void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts, size_t* z);
 void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s);
 int64_t apply_bytes(const Matrix& M, int i);
 // ---- solve.cu
@@ -160,4 +165,11 @@ int64_t level_size(const Matrix& M, int i);
 void exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, Matrix& M);
 void radix_sort_u64(uint64_t* keys, int* vals, int n, int bits, Matrix& M, cudaStream_t s);
 
+bool is_device_pointer(const void* p);
+
 }  // namespace h2mg
+
+// The opaque handle behind h2mg_matrix.
+struct h2mg_matrix_s {
+  h2mg::Matrix M;
+};
