@@ -271,6 +271,8 @@ def main():
     infos = []
     A.profile(1)
     l0 = pkg.H2Matrix.launch_count()
+    if os.environ.get("H2MG_BENCH_REPORT_LAUNCHES"):
+        print(f"launches before the timed region: {l0}", file=sys.stderr, flush=True)
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(a.steps):

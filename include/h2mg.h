@@ -134,6 +134,22 @@ h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int6
 h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int64_t ld,
                        const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream);
 
+/* Build the H2 matrix of another kernel on the same points with the same cluster
+ * tree, block partition, Chebyshev nodes and orthonormalisation factors as A
+ * (Sec. 3.1 form with A's bases; only D and the couplings S = R k'(xi, xi) R^T
+ * change). With H2MG_K_DMATERN32_DL (length = A's length, nugget 0) this is
+ * d A / d length of a Matern-3/2 H2 matrix: since the interpolation bases do not
+ * depend on the kernel's parameters, it is the exact derivative of A's H2 form.
+ * The result supports products only (h2mg_apply, h2mg_apply_level at level 1);
+ * h2mg_solve on it returns INVALID_ARG. It refers to A's device structures:
+ * destroy it before A. Weights and diagonal overrides of k are not supported
+ * (INVALID_ARG). */
+h2mg_status h2mg_build_sibling(h2mg_matrix A, const h2mg_kernel* k, void* stream, h2mg_matrix* out);
+
+/* *out = x^T y for n float64 values (host or device vectors), reduced on the GPU
+ * with the library's deterministic two-pass sum; synchronises the stream. */
+h2mg_status h2mg_dot(const double* x, const double* y, int64_t n, double* out, void* stream);
+
 /* Free every device buffer of the handle. NULL is accepted. */
 h2mg_status h2mg_destroy(h2mg_matrix A);
 
@@ -225,13 +241,13 @@ h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* m
  * cudaFree or allocating library routine: its workspace lives in one fixed array of
  * H2MG_NOALLOC_SCRATCH_BYTES bytes of device memory that every GPU loading this
  * library holds until the process exits. Matrices whose product needs more scratch
- * than that are rejected with UNSUPPORTED (about 2^16 points in 3-D with leaf 64 and
- * 4x4x4 nodes fit). The first call on a device looks up the array's address with
+ * than that are rejected with UNSUPPORTED (the product needs about 64 bytes per
+ * point: some 2^18 points fit). The first call on a device looks up the array's address with
  * that device current; make that first call before any stream capture. All calls
  * share the array and it keeps the last call's contents: calls whose work overlaps
  * on the GPU (different streams, or different host threads) race and give wrong
  * results. */
-#define H2MG_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define H2MG_NOALLOC_SCRATCH_BYTES (16u << 20)
 h2mg_status h2mg_apply_noalloc(h2mg_matrix A, const double* x, double* y, void* stream);
 
 #ifdef __cplusplus

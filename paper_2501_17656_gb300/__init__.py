@@ -15,7 +15,8 @@ import os
 
 import numpy as np
 
-__all__ = ["H2Matrix", "KERNELS", "SolveInfo", "H2MGError", "load_library", "library_path"]
+__all__ = ["H2Matrix", "KERNELS", "SolveInfo", "H2MGError", "load_library", "library_path", "dot",
+           "MaternLoss"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libh2mg.so")
@@ -35,7 +36,7 @@ X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5)
 EXPORTED = ["h2mg_build", "h2mg_apply", "h2mg_solve", "h2mg_destroy", "h2mg_error_string",
             "h2mg_last_error", "h2mg_query", "h2mg_export", "h2mg_apply_level",
             "h2mg_coarse_solve", "h2mg_smooth", "h2mg_vcycle", "h2mg_launch_count", "h2mg_profile",
-            "h2mg_transfer", "h2mg_apply_noalloc"]
+            "h2mg_transfer", "h2mg_apply_noalloc", "h2mg_build_sibling", "h2mg_dot"]
 
 
 class H2MGError(RuntimeError):
@@ -104,6 +105,8 @@ def load_library(build_if_missing: bool = False):
     lib.h2mg_launch_count.argtypes = []
     lib.h2mg_transfer.argtypes = [vp, ci, ci, vp, vp, vp]
     lib.h2mg_apply_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.h2mg_build_sibling.argtypes = [vp, ctypes.POINTER(_Kernel), vp, ctypes.POINTER(vp)]
+    lib.h2mg_dot.argtypes = [vp, vp, i64, ctypes.POINTER(cd), vp]
     lib.h2mg_profile.argtypes = [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(cd), ctypes.POINTER(cd)]
     for name in EXPORTED:
         if name not in ("h2mg_error_string", "h2mg_last_error", "h2mg_launch_count"):
@@ -153,6 +156,14 @@ def _like(x, n):
     return torch.zeros(n, dtype=torch.float64, device=x.device)
 
 
+def dot(x, y) -> float:
+    """x^T y (float64) reduced by the library on the GPU."""
+    out = ctypes.c_double()
+    n = int(x.shape[0])
+    _check(load_library().h2mg_dot(_ptr(x), _ptr(y), n, ctypes.byref(out), _stream()))
+    return float(out.value)
+
+
 class H2Matrix:
     """An H2 matrix built on the GPU from points and a kernel (Sec. 3.1 of the paper),
     with its H2-MG multigrid hierarchy (Sec. 3.3)."""
@@ -175,6 +186,18 @@ class H2Matrix:
         self._h = h
         self.n, self.dim = n, dim
         self._keep = None
+
+    # ----------------------------------------------------------------- siblings
+    def sibling(self, kernel: str, length: float = 1.0, nugget: float = 0.0, degree: int = 2) -> "H2Matrix":
+        """The H2 matrix of another kernel with this matrix's tree, partition, nodes and
+        bases (products only); e.g. ``sibling("dmatern32_dl", length)`` = dA/dlength."""
+        k = _Kernel(KERNELS[kernel], float(length), float(nugget), int(degree), None, None)
+        h = ctypes.c_void_p()
+        _check(self._lib.h2mg_build_sibling(self._h, ctypes.byref(k), _stream(), ctypes.byref(h)))
+        out = H2Matrix.__new__(H2Matrix)
+        out._lib, out._h, out.n, out.dim, out._keep = self._lib, h, self.n, self.dim, None
+        out._base = self          # the sibling uses this matrix's device structures
+        return out
 
     # ----------------------------------------------------------------- lifetime
     def close(self):
@@ -291,3 +314,49 @@ class H2Matrix:
         if st != 0 and (raise_on_fail or st not in (5,)):
             _check(st)
         return x, info
+
+
+# --------------------------------------------------------------------------- adjoint
+class MaternLoss:
+    """L(y, b, length, nugget) = 1/2 y^T K^{-1} y + 1^T K^{-1} b for the Matern-3/2 kernel
+    matrix K = (1 + sqrt3 r/l) exp(-sqrt3 r/l) + s I in H2 form, with gradients by the
+    adjoint method: dL/dy = K^{-1} y, dL/db = K^{-1} 1 (one extra H2-MG solve, K being
+    symmetric), dL/dtheta = -1/2 a^T (dK/dtheta) a - w^T (dK/dtheta) x with a = K^{-1} y,
+    x = K^{-1} b, w = K^{-1} 1; dK/dl is the H2 sibling of K with the derivative kernel
+    and dK/ds = I. Only the solution vectors are kept between forward and backward."""
+
+    @staticmethod
+    def apply(points, y, b, length, nugget, leaf=64, q=4, eta=1.0, tol=1e-12, max_cycles=200,
+              outer="fcg", n_f=1, n_c=40):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, y_, b_, l_, s_):
+                K = H2Matrix(points, "matern32", length=float(l_), nugget=float(s_), leaf=leaf, q=q, eta=eta)
+                kw = dict(tol=tol, max_cycles=max_cycles, outer=outer, n_f=n_f, n_c=n_c)
+                a, _ = K.solve(y_.detach().contiguous(), **kw)
+                x, _ = K.solve(b_.detach().contiguous(), **kw)
+                ones = torch.ones_like(x)
+                loss = 0.5 * dot(y_.detach().contiguous(), a) + dot(x, ones)
+                ctx.K, ctx.kw, ctx.l = K, kw, float(l_)
+                ctx.save_for_backward(a, x)
+                return torch.tensor(loss, dtype=torch.float64, device=y_.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                a, x = ctx.saved_tensors
+                K = ctx.K
+                ones = torch.ones_like(x)
+                w, _ = K.solve(ones, **ctx.kw)
+                dK = K.sibling("dmatern32_dl", length=ctx.l)
+                dKa, dKx = dK.apply(a), dK.apply(x)
+                dl = -0.5 * dot(a, dKa) - dot(w, dKx)
+                ds = -0.5 * dot(a, a) - dot(w, x)
+                dK.close()
+                gv = float(g)
+                dev = a.device
+                return (gv * a, gv * w, torch.tensor(gv * dl, dtype=torch.float64, device=dev),
+                        torch.tensor(gv * ds, dtype=torch.float64, device=dev))
+
+        return _Fn.apply(y, b, length, nugget)

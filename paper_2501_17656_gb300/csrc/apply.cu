@@ -30,6 +30,8 @@ struct Ar;
 template <>
 struct Ar<FMT_F64> {
   static constexpr int V = 2;
+  using yo_t = double;       // type of the atomically accumulated row outputs
+  __device__ static yo_t to_yo(double a) { return a; }
   using vec_t = double;
   using mel_t = double;
   using acc_t = double;
@@ -51,6 +53,8 @@ struct Ar<FMT_F64> {
 template <>
 struct Ar<FMT_DF> {
   static constexpr int V = 2;
+  using yo_t = double;
+  __device__ static yo_t to_yo(float2 a) { return (double)a.x + (double)a.y; }
   using vec_t = float2;
   using mel_t = float2;
   using acc_t = float2;
@@ -80,6 +84,8 @@ struct Ar<FMT_DF> {
 template <>
 struct Ar<FMT_F32> {
   static constexpr int V = 4;
+  using yo_t = float;
+  __device__ static yo_t to_yo(float a) { return a; }
   using vec_t = float;
   using mel_t = float;
   using acc_t = float;
@@ -101,15 +107,18 @@ struct Ar<FMT_F32> {
 };
 
 // ----------------------------------------------------------------------------- block GEMV
-// One CTA (8 warps) per block row t of a symmetric upper-stored block operator.
-// yrow[t] = sum_e B_e x_col(e);  z[e] = B_e^T x_t for every off-diagonal entry e.
+// One CTA (8 warps) per block row t of a symmetric upper-stored block operator:
+// yrow[t] += sum_e B_e x_col(e) and, for every off-diagonal entry e = (t, s),
+// yrow[s] += B_e^T x_t. All contributions are atomic adds (FP64 for the F64 and DF
+// copies, FP32 for the F32 copy) into a row buffer zeroed before the launch, so the
+// summation order, and the last bits of a sum, may differ from run to run. When the
+// operator has few rows, each row is split over `split` CTAs (strided entries).
 template <int K, int FMT>
 __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
                                                 const int* __restrict__ col,
                                                 const void* const* __restrict__ blk,
                                                 const typename Ar<FMT>::vec_t* __restrict__ x,
-                                                typename Ar<FMT>::vec_t* __restrict__ yrow,
-                                                typename Ar<FMT>::vec_t* __restrict__ z) {
+                                                typename Ar<FMT>::yo_t* __restrict__ yrow, int split) {
   using A = Ar<FMT>;
   using vec_t = typename A::vec_t;
   using mel_t = typename A::mel_t;
@@ -120,7 +129,7 @@ __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
   constexpr int V = A::V, P = 8 / V;
   __shared__ acc_t red[8][K];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int row = blockIdx.x;
+  const int row = blockIdx.x / split, part = blockIdx.x % split;
   const int rb = 8 * (lane % LPC), cl = lane / LPC;
   vec_t xt[8];
 #pragma unroll
@@ -129,7 +138,7 @@ __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
 #pragma unroll
   for (int r = 0; r < 8; ++r) ya[r] = A::zero();
   const int e0 = rowptr[row], e1 = rowptr[row + 1];
-  for (int e = e0 + w; e < e1; e += 8) {
+  for (int e = e0 + part * 8 + w; e < e1; e += 8 * split) {
     const int s = col[e];
     const ld_t* B = (const ld_t*)blk[e];
     const vec_t* xs = x + (int64_t)s * K;
@@ -174,11 +183,11 @@ __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
             }
           }
           const int tt = lane & (CH - 1);
-          z[(int64_t)e * K + cl + CPP * (ch * CH + tt)] = A::out(zc[0]);
+          atomicAdd(yrow + (int64_t)s * K + cl + CPP * (ch * CH + tt), A::to_yo(A::out(zc[0])));
         } else {
 #pragma unroll
           for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0], A::shfl(zc[0], h));
-          if ((lane % LPC) == 0) z[(int64_t)e * K + cl + CPP * (ch * CH)] = A::out(zc[0]);
+          if ((lane % LPC) == 0) atomicAdd(yrow + (int64_t)s * K + cl + CPP * (ch * CH), A::to_yo(A::out(zc[0])));
         }
       }
     }
@@ -198,7 +207,7 @@ __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
     acc_t s = red[0][i];
 #pragma unroll
     for (int ww = 1; ww < 8; ++ww) A::add(s, red[ww][i]);
-    yrow[(int64_t)row * K + i] = A::out(s);
+    atomicAdd(yrow + (int64_t)row * K + i, A::to_yo(A::out(s)));
   }
 }
 
@@ -235,62 +244,163 @@ __global__ void k_up_leaf(const BT* __restrict__ UT, int KD, int KC,
   }
 }
 
-// x_hat(P)[b] = sum_{c in children(P)} sum_a E'_c[a, b] x_hat(c)[a]  (ET = E'^T)
-template <int FMT, class BT>
-__global__ void k_up(const BT* __restrict__ ET, int KC, const typename Ar<FMT>::vec_t* __restrict__ xch,
-                     typename Ar<FMT>::vec_t* __restrict__ xpar) {
-  __shared__ double xs[128];
-  int p = blockIdx.x;
-  for (int i = threadIdx.x; i < 2 * KC; i += blockDim.x) xs[i] = Ar<FMT>::to_d(xch[(int64_t)2 * p * KC + i]);
-  __syncthreads();
-  for (int b = threadIdx.x; b < KC; b += blockDim.x) {
-    double acc = 0.0;
-    for (int c = 0; c < 2; ++c) {
-      const BT* E = ET + (int64_t)(2 * p + c) * KC * KC;
-      for (int a = 0; a < KC; ++a) acc += (double)E[b + a * KC] * xs[c * KC + a];
-    }
-    xpar[(int64_t)p * KC + b] = Ar<FMT>::from_d(acc);
-  }
-}
-
-// y_hat(c)[a] = yrow(c)[a] + sum_{e in gather(c)} z[e][a] + sum_b E'_c[a, b] y_hat(parent)[b]
-// Writes the product format (yc) or, for the output level, float64 (yout).
-template <int FMT, class BT>
-__global__ void k_down_final(int slot_base, int KC, const typename Ar<FMT>::vec_t* __restrict__ yrow,
-                             const int* __restrict__ gptr, const int* __restrict__ gent,
-                             const typename Ar<FMT>::vec_t* __restrict__ z, const BT* __restrict__ E,
-                             const typename Ar<FMT>::vec_t* __restrict__ ypar,
-                             typename Ar<FMT>::vec_t* __restrict__ yc, double* __restrict__ yout) {
+// Transfer passes as block products. Every orthonormal transfer E'_c (K x K, rows =
+// child coefficients, columns = parent coefficients) is stored swizzled like the
+// blocks of k_bsgemv, and one warp streams one transfer with the same lane layout:
+// the upward pass uses the transposed product E'_c^T x_c (reduce-scatter over the
+// lanes that share a column), the downward pass the row product E'_c y_parent.
+template <int K, int FMT>
+__global__ void __launch_bounds__(256) k_up_blk(const void* __restrict__ Epool,
+                                                const typename Ar<FMT>::vec_t* __restrict__ xch,
+                                                typename Ar<FMT>::vec_t* __restrict__ xpar, int nch) {
   using A = Ar<FMT>;
-  __shared__ double ps[64];
-  int c = blockIdx.x;
-  int sl = slot_base + c;
-  if (E)
-    for (int i = threadIdx.x; i < KC; i += blockDim.x) ps[i] = A::to_d(ypar[(int64_t)(c >> 1) * KC + i]);
-  __syncthreads();
-  for (int a = threadIdx.x; a < KC; a += blockDim.x) {
-    typename A::acc_t acc = yrow[(int64_t)sl * KC + a];
-    for (int g = gptr[sl]; g < gptr[sl + 1]; ++g) A::add(acc, z[(int64_t)gent[g] * KC + a]);
-    double v = A::to_d(A::out(acc));
-    if (E) {
-      const BT* Ec = E + (int64_t)c * KC * KC;
-      double t = 0.0;
-      for (int b = 0; b < KC; ++b) t += (double)Ec[a + b * KC] * ps[b];
-      v += t;
+  using vec_t = typename A::vec_t;
+  using mel_t = typename A::mel_t;
+  using acc_t = typename A::acc_t;
+  using ld_t = typename A::ld_t;
+  constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
+  constexpr int CH = T < LPC ? T : LPC;
+  constexpr int V = A::V, P = 8 / V;
+  __shared__ acc_t v[8][K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 8 + w;
+  const int rb = 8 * (lane % LPC), cl = lane / LPC;
+  if (c < nch) {
+    vec_t xt[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) xt[r] = xch[(int64_t)c * K + rb + r];
+    const ld_t* B = (const ld_t*)((const char*)Epool + (int64_t)c * K * K * (FMT == FMT_F32 ? 4 : 8));
+#pragma unroll 1
+    for (int ch = 0; ch < T / CH; ++ch) {
+      acc_t zc[CH];
+#pragma unroll
+      for (int tt = 0; tt < CH; ++tt) {
+        const int t = ch * CH + tt;
+        mel_t m[8];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          ld_t q = __ldg(B + (t * P + k) * 32 + lane);
+          A::decode(q, m + k * V);
+        }
+        acc_t zz = A::zero();
+#pragma unroll
+        for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r]);
+        zc[tt] = zz;
+      }
+      if (CH == LPC) {
+#pragma unroll
+        for (int h = CH / 2; h >= 1; h >>= 1) {
+          const bool up = (lane & h) != 0;
+#pragma unroll
+          for (int j = 0; j < h; ++j) {
+            acc_t send = up ? zc[j] : zc[j + h];
+            acc_t keep = up ? zc[j + h] : zc[j];
+            A::add(keep, A::shfl(send, h));
+            zc[j] = keep;
+          }
+        }
+        v[w][cl + CPP * (ch * CH + (lane & (CH - 1)))] = zc[0];
+      } else {
+#pragma unroll
+        for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0], A::shfl(zc[0], h));
+        if ((lane % LPC) == 0) v[w][cl + CPP * (ch * CH)] = zc[0];
+      }
     }
-    if (yout)
-      yout[(int64_t)c * KC + a] = v;
-    else
-      yc[(int64_t)sl * KC + a] = A::from_d(v);
+  }
+  __syncthreads();
+  if (c < nch && (w & 1) == 0) {
+    const int p = c >> 1;
+    for (int j = lane; j < K; j += 32) {
+      acc_t s = v[w][j];
+      A::add(s, v[w + 1][j]);
+      xpar[(int64_t)p * K + j] = A::out(s);
+    }
   }
 }
 
-// y(point) = yrowD + gathered transposes + U y_hat(leaf), scattered to user order.
+template <int K, int FMT>
+__global__ void __launch_bounds__(256) k_down_blk(int slot_base, int ncl,
+                                                  const typename Ar<FMT>::yo_t* __restrict__ yrow,
+                                                  const void* __restrict__ Epool,
+                                                  const typename Ar<FMT>::vec_t* __restrict__ ypar,
+                                                  typename Ar<FMT>::vec_t* __restrict__ yc,
+                                                  double* __restrict__ yout) {
+  using A = Ar<FMT>;
+  using vec_t = typename A::vec_t;
+  using mel_t = typename A::mel_t;
+  using acc_t = typename A::acc_t;
+  using ld_t = typename A::ld_t;
+  constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
+  constexpr int V = A::V, P = 8 / V;
+  __shared__ acc_t s[8][K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 8 + w;
+  if (c >= ncl) return;
+  const int sl = slot_base + c;
+  if (Epool) {
+    const int rb = 8 * (lane % LPC), cl = lane / LPC;
+    acc_t ya[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ya[r] = A::zero();
+    const ld_t* B = (const ld_t*)((const char*)Epool + (int64_t)c * K * K * (FMT == FMT_F32 ? 4 : 8));
+    const vec_t* yp = ypar + (int64_t)(c >> 1) * K;
+#pragma unroll 4
+    for (int t = 0; t < T; ++t) {
+      mel_t m[8];
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        ld_t q = __ldg(B + (t * P + k) * 32 + lane);
+        A::decode(q, m + k * V);
+      }
+      const vec_t xv = yp[cl + CPP * t];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) A::fma(ya[r], m[r], xv);
+    }
+#pragma unroll
+    for (int h = LPC; h < 32; h <<= 1)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) A::add(ya[r], A::shfl(ya[r], h));
+    if (lane < LPC)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) s[w][rb + r] = ya[r];
+    __syncwarp();
+  }
+  for (int a = lane; a < K; a += 32) {
+    acc_t acc = A::from_d((double)yrow[(int64_t)sl * K + a]);
+    if (Epool) A::add(acc, s[w][a]);
+    vec_t o = A::out(acc);
+    if (yout)
+      yout[(int64_t)c * K + a] = A::to_d(o);
+    else
+      yc[(int64_t)sl * K + a] = o;
+  }
+}
+
+// natural column-major K x K blocks (float64) -> swizzled blocks in a format
+__global__ void k_swizzle_blocks(const double* __restrict__ in, int K, void* __restrict__ out, int fmt) {
+  int64_t b = blockIdx.x;
+  int V = fmt == FMT_F32 ? 4 : 2, LPC = K / 8, CPP = 32 / LPC, P = 8 / V;
+  for (int pos = threadIdx.x; pos < K * K; pos += blockDim.x) {
+    int sub = pos % V, ln = (pos / V) % 32, tk = pos / (V * 32);
+    int t = tk / P, k = tk % P;
+    int i = 8 * (ln % LPC) + k * V + sub, j = t * CPP + ln / LPC;
+    double v = in[b * K * K + i + (int64_t)j * K];
+    int64_t idx = b * K * K + pos;
+    if (fmt == FMT_F64) {
+      ((double*)out)[idx] = v;
+    } else if (fmt == FMT_DF) {
+      float h = __double2float_rn(v);
+      ((float2*)out)[idx] = make_float2(h, __double2float_rn(v - (double)h));
+    } else {
+      ((float*)out)[idx] = __double2float_rn(v);
+    }
+  }
+}
+
+// y(point) = yrowD + U y_hat(leaf), scattered to user order.
 template <int FMT, class BT>
-__global__ void k_leaf_final(int KD, int KC, const typename Ar<FMT>::vec_t* __restrict__ yrow,
-                             const int* __restrict__ gptr, const int* __restrict__ gent,
-                             const typename Ar<FMT>::vec_t* __restrict__ z, const BT* __restrict__ U,
-                             const typename Ar<FMT>::vec_t* __restrict__ yleaf,
+__global__ void k_leaf_final(int KD, int KC, const typename Ar<FMT>::yo_t* __restrict__ yrow,
+                             const BT* __restrict__ U, const typename Ar<FMT>::vec_t* __restrict__ yleaf,
                              const int* __restrict__ leafoff, const int* __restrict__ perm,
                              double* __restrict__ y) {
   using A = Ar<FMT>;
@@ -301,9 +411,7 @@ __global__ void k_leaf_final(int KD, int KC, const typename Ar<FMT>::vec_t* __re
   __syncthreads();
   int p0 = leafoff[j], nj = leafoff[j + 1] - p0;
   for (int i = threadIdx.x; i < nj; i += blockDim.x) {
-    typename A::acc_t acc = yrow[(int64_t)j * KD + i];
-    for (int g = gptr[j]; g < gptr[j + 1]; ++g) A::add(acc, z[(int64_t)gent[g] * KD + i]);
-    double v = A::to_d(A::out(acc));
+    double v = (double)yrow[(int64_t)j * KD + i];
     if (U) {
       const BT* Uj = U + (int64_t)j * KD * KC;
       double t = 0.0;
@@ -379,19 +487,10 @@ static SymOp upload_op(Matrix& M, const OpHost& H, int K, const void* pool0, con
   }
   op.blk = (const void**)up(p.data(), sizeof(void*) * p.size());
   op.blk32 = (const void**)up(p32.data(), sizeof(void*) * p32.size());
-  // gather lists: entries (t, s), s > t, collected by s
-  std::vector<int> gcnt(op.nrows + 1, 0);
+  int64_t noff = 0;
   for (int t = 0; t < op.nrows; ++t)
-    for (int e = H.rowptr[t]; e < H.rowptr[t + 1]; ++e)
-      if (H.col[e] != t) gcnt[H.col[e] + 1]++;
-  for (int i = 0; i < op.nrows; ++i) gcnt[i + 1] += gcnt[i];
-  std::vector<int> gent(std::max(gcnt[op.nrows], 1)), fill(gcnt.begin(), gcnt.end() - 1);
-  for (int t = 0; t < op.nrows; ++t)
-    for (int e = H.rowptr[t]; e < H.rowptr[t + 1]; ++e)
-      if (H.col[e] != t) gent[fill[H.col[e]]++] = e;
-  op.noff = gcnt[op.nrows];
-  op.gptr = (int*)up(gcnt.data(), sizeof(int) * gcnt.size());
-  op.gent = (int*)up(gent.data(), sizeof(int) * gent.size());
+    for (int e = H.rowptr[t]; e < H.rowptr[t + 1]; ++e) noff += (H.col[e] != t);
+  op.noff = noff;
   return op;
 }
 
@@ -447,7 +546,6 @@ void setup_operators(Matrix& M) {
     M.opD = upload_op(M, H, M.KD, M.poolD.p, nullptr, M.poolD32.p, nullptr);
   }
   M.opC.assign(M.lev + 1, SymOp{});
-  size_t zmax = (size_t)M.opD.nnz * M.KD;
   if (M.tstar >= 0) {
     for (int i = 1; i <= M.lev; ++i) {
       if (M.apply_only && i > 1) break;
@@ -456,22 +554,33 @@ void setup_operators(Matrix& M) {
       const void* pP = (i >= 2) ? M.poolP[i].p : nullptr;
       const void* pP32 = (i >= 2 && M.with_f32) ? M.poolP32[i].p : nullptr;
       M.opC[i] = upload_op(M, H, M.KC, M.poolS.p, pP, M.with_f32 ? M.poolS32.p : nullptr, pP32);
-      size_t zi = (size_t)M.opC[i].nnz * M.KC + (i == 1 ? (size_t)M.opD.nnz * M.KD : 0);
-      zmax = std::max(zmax, zi);
     }
-    // transposed copies of the transfers and leaf bases (coalesced upward pass)
+    // transposed copies of the transfers and leaf bases (coalesced upward pass) and the
+    // swizzled transfer pools; a sibling matrix already has its base's
     size_t nu = (size_t)(1 << L), ne = (size_t)M.nslots();
-    double* UT = (double*)M.alloc(sizeof(double) * nu * M.KD * M.KC);
-    double* ET = (double*)M.alloc(sizeof(double) * ne * M.KC * M.KC);
-    { k_transpose_blocks<<<(int)nu, 256, 0, s>>>(M.d_U, M.KD, M.KC, UT); ::h2mg::count_launch(); }
-    { k_transpose_blocks<<<(int)ne, 256, 0, s>>>(M.d_E, M.KC, M.KC, ET); ::h2mg::count_launch(); }
-    H2_LAUNCH_CHECK();
-    M.d_UT = UT;
-    M.d_ET = ET;
+    if (!M.d_UT) {
+      double* UT = (double*)M.alloc(sizeof(double) * nu * M.KD * M.KC);
+      double* ET = (double*)M.alloc(sizeof(double) * ne * M.KC * M.KC);
+      { k_transpose_blocks<<<(int)nu, 256, 0, s>>>(M.d_U, M.KD, M.KC, UT); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+      { k_transpose_blocks<<<(int)ne, 256, 0, s>>>(M.d_E, M.KC, M.KC, ET); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+      M.d_UT = UT;
+      M.d_ET = ET;
+      M.poolE.bytes = ne * M.KC * M.KC * fmt_bytes(M.fmt);
+      M.poolE.p = M.alloc(M.poolE.bytes);
+      { k_swizzle_blocks<<<(int)ne, 256, 0, s>>>(M.d_E, M.KC, M.poolE.p, M.fmt); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+    }
     if (M.with_f32) {
+      M.poolE32.bytes = ne * M.KC * M.KC * 4;
+      M.poolE32.p = M.alloc(M.poolE32.bytes);
+      { k_swizzle_blocks<<<(int)ne, 256, 0, s>>>(M.d_E, M.KC, M.poolE32.p, FMT_F32); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
       float* UT32 = (float*)M.alloc(sizeof(float) * nu * M.KD * M.KC);
       float* ET32 = (float*)M.alloc(sizeof(float) * ne * M.KC * M.KC);
       { k_transpose_blocks32<<<(int)nu, 256, 0, s>>>(M.d_U32, M.KD, M.KC, UT32); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
       { k_transpose_blocks32<<<(int)ne, 256, 0, s>>>(M.d_E32, M.KC, M.KC, ET32); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
       M.d_UT32 = UT32;
@@ -485,16 +594,18 @@ void setup_operators(Matrix& M) {
   M.wyc.p = M.alloc(8 * ncoef);
   M.wxp.p = M.alloc(8 * npts);
   M.wyp.p = M.alloc(8 * npts);
-  M.wz.bytes = 8 * std::max<size_t>(zmax, 1);
-  M.wz.p = M.alloc(M.wz.bytes);
   H2_CUDA(cudaStreamSynchronize(s));
 }
 
 template <int FMT>
-static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, void* yrow, void* z,
-                          cudaStream_t s) {
+static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, void* yrow, cudaStream_t s) {
   using vt = typename Ar<FMT>::vec_t;
+  using yt = typename Ar<FMT>::yo_t;
   if (op.nrows == 0) return;
+  H2_CUDA(cudaMemsetAsync(yrow, 0, sizeof(yt) * (size_t)op.nrows * op.K, s));
+  // enough CTAs to fill the GPU when the operator has few block rows
+  const int split = std::max(1, std::min(16, ceil_div(2048, op.nrows)));
+  const int grid = op.nrows * split;
   const void* const* blk = f32 ? op.blk32 : op.blk;
   Profile& P = M.prof;
   if (P.on) {
@@ -509,13 +620,13 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
   }
   switch (op.K) {
     case 16:
-      { k_bsgemv<16, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z); ::h2mg::count_launch(); }
+      { k_bsgemv<16, FMT><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
       break;
     case 32:
-      { k_bsgemv<32, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z); ::h2mg::count_launch(); }
+      { k_bsgemv<32, FMT><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
       break;
     case 64:
-      { k_bsgemv<64, FMT><<<op.nrows, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (vt*)yrow, (vt*)z); ::h2mg::count_launch(); }
+      { k_bsgemv<64, FMT><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
       break;
     default:
       throw Error{H2MG_ERR_UNSUPPORTED, "block size not supported"};
@@ -528,42 +639,65 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
   }
 }
 
+template <int FMT>
+static void launch_up(const void* Epool, int KC, const void* xch, void* xpar, int nch, cudaStream_t s) {
+  using vt = typename Ar<FMT>::vec_t;
+  int grid = ceil_div(nch, 8);
+  switch (KC) {
+    case 16: { k_up_blk<16, FMT><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
+    case 32: { k_up_blk<32, FMT><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
+    default: { k_up_blk<64, FMT><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
+  }
+  H2_LAUNCH_CHECK();
+}
+
+template <int FMT>
+static void launch_down(int slot_base, int KC, int ncl, const void* yrow, const void* Epool, const void* ypar,
+                        void* yc, double* yout, cudaStream_t s) {
+  using vt = typename Ar<FMT>::vec_t;
+  using yt = typename Ar<FMT>::yo_t;
+  int grid = ceil_div(ncl, 8);
+  switch (KC) {
+    case 16: { k_down_blk<16, FMT><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout); ::h2mg::count_launch(); } break;
+    case 32: { k_down_blk<32, FMT><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout); ::h2mg::count_launch(); } break;
+    default: { k_down_blk<64, FMT><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout); ::h2mg::count_launch(); } break;
+  }
+  H2_LAUNCH_CHECK();
+}
+
 template <int FMT, class BT>
 static void apply_impl(Matrix& M, int i, const double* x, double* y, cudaStream_t s, const BT* U,
                        const BT* UT, const BT* E, const BT* ET, const ApplyWork* ws = nullptr) {
   using vt = typename Ar<FMT>::vec_t;
   const int L = M.L, KC = M.KC, KD = M.KD, ts = M.tstar;
   const bool f32 = (FMT == FMT_F32);
+  using yt = typename Ar<FMT>::yo_t;
   vt* xc = (vt*)(ws ? ws->xc : M.wx.p);
-  vt* yr = (vt*)(ws ? ws->yr : M.wyrow.p);
+  yt* yr = (yt*)(ws ? ws->yr : M.wyrow.p);
   vt* yc = (vt*)(ws ? ws->yc : M.wyc.p);
-  vt* z = (vt*)(ws ? ws->z : M.wz.p);
+  const char* epool = (const char*)(FMT == FMT_F32 ? M.poolE32.p : M.poolE.p);
+  const size_t eb = FMT == FMT_F32 ? 4 : 8;
   if (i == 1) {
     vt* xp = (vt*)(ws ? ws->xp : M.wxp.p);
-    vt* yp = (vt*)(ws ? ws->yp : M.wyp.p);
+    yt* yp = (yt*)(ws ? ws->yp : M.wyp.p);
     { k_pts_in<FMT><<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, xp); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
-    vt* zc = z + (size_t)M.opD.nnz * KD;
     if (ts >= 0) {
       { k_up_leaf<FMT, BT><<<1 << L, std::max(KC, 32), 0, s>>>(UT, KD, KC, xp, xc + (size_t)M.slot0(L) * KC); ::h2mg::count_launch(); }
       for (int ell = L - 1; ell >= ts; --ell)
-        { k_up<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(ET + (size_t)M.slot0(ell + 1) * KC * KC, KC,
-                                                            xc + (size_t)M.slot0(ell + 1) * KC,
-                                                            xc + (size_t)M.slot0(ell) * KC); ::h2mg::count_launch(); }
-      H2_LAUNCH_CHECK();
+        launch_up<FMT>(epool + (size_t)M.slot0(ell + 1) * KC * KC * eb, KC, xc + (size_t)M.slot0(ell + 1) * KC,
+                       xc + (size_t)M.slot0(ell) * KC, 1 << (ell + 1), s);
     }
-    launch_bsgemv<FMT>(M, M.opD, f32, xp, yp, z, s);
+    launch_bsgemv<FMT>(M, M.opD, f32, xp, yp, s);
     if (ts >= 0) {
-      launch_bsgemv<FMT>(M, M.opC[1], f32, xc, yr, zc, s);
+      launch_bsgemv<FMT>(M, M.opC[1], f32, xc, yr, s);
       for (int ell = ts; ell <= L; ++ell)
-        { k_down_final<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(
-            M.slot0(ell), KC, yr, M.opC[1].gptr, M.opC[1].gent, zc,
-            ell > ts ? E + (size_t)M.slot0(ell) * KC * KC : nullptr,
-            ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, nullptr); ::h2mg::count_launch(); }
-      H2_LAUNCH_CHECK();
+        launch_down<FMT>(M.slot0(ell), KC, 1 << ell, yr,
+                         ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr,
+                         ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, nullptr, s);
     }
     { k_leaf_final<FMT, BT><<<1 << L, std::max(KD, 32), 0, s>>>(
-        KD, KC, yp, M.opD.gptr, M.opD.gent, z, ts >= 0 ? U : nullptr,
+        KD, KC, yp, ts >= 0 ? U : nullptr,
         ts >= 0 ? yc + (size_t)M.slot0(L) * KC : nullptr, M.d_leafoff, M.d_perm, y); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     return;
@@ -573,17 +707,13 @@ static void apply_impl(Matrix& M, int i, const double* x, double* y, cudaStream_
   { k_coef_in<FMT><<<ceil_div(nm, 256), 256, 0, s>>>(x, nm, xc + (size_t)M.slot0(m) * KC); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   for (int ell = m - 1; ell >= ts; --ell)
-    { k_up<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(ET + (size_t)M.slot0(ell + 1) * KC * KC, KC,
-                                                        xc + (size_t)M.slot0(ell + 1) * KC,
-                                                        xc + (size_t)M.slot0(ell) * KC); ::h2mg::count_launch(); }
-  H2_LAUNCH_CHECK();
-  launch_bsgemv<FMT>(M, M.opC[i], f32, xc, yr, z, s);
+    launch_up<FMT>(epool + (size_t)M.slot0(ell + 1) * KC * KC * eb, KC, xc + (size_t)M.slot0(ell + 1) * KC,
+                   xc + (size_t)M.slot0(ell) * KC, 1 << (ell + 1), s);
+  launch_bsgemv<FMT>(M, M.opC[i], f32, xc, yr, s);
   for (int ell = ts; ell <= m; ++ell)
-    { k_down_final<FMT, BT><<<1 << ell, std::max(KC, 32), 0, s>>>(
-        M.slot0(ell), KC, yr, M.opC[i].gptr, M.opC[i].gent, z,
-        ell > ts ? E + (size_t)M.slot0(ell) * KC * KC : nullptr,
-        ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, ell == m ? y : nullptr); ::h2mg::count_launch(); }
-  H2_LAUNCH_CHECK();
+    launch_down<FMT>(M.slot0(ell), KC, 1 << ell, yr,
+                     ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr,
+                     ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, ell == m ? y : nullptr, s);
 }
 
 void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s) {
@@ -607,12 +737,9 @@ void apply_level1_ws(Matrix& M, const double* x, double* y, cudaStream_t s, cons
 }
 
 // Bytes of each workspace region of the level-1 product.
-void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts, size_t* z) {
+void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts) {
   *coef = 8 * (size_t)std::max(M.nslots(), 1) * M.KC;
   *pts = 8 * (size_t)(1 << M.L) * M.KD;
-  size_t zz = (size_t)M.opD.nnz * M.KD;
-  if (M.tstar >= 0) zz += (size_t)M.opC[1].nnz * M.KC;
-  *z = 8 * std::max<size_t>(zz, 1);
 }
 
 // Algorithmic bytes of one A_i apply in the primary format: every stored block once,

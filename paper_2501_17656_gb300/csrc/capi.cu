@@ -131,6 +131,29 @@ static void build_all(Matrix& M, const double* points, const h2mg_kernel* k, con
   H2_CUDA(cudaStreamSynchronize(s));
 }
 
+// A sibling shares the base's tree, partition, bases and transfers (not owned) and
+// owns only its block pools, operators and workspaces.
+static void build_sibling(Matrix& B, const Matrix& A, const h2mg_kernel* k) {
+  cudaStream_t s = B.stream;
+  B.n = A.n; B.dim = A.dim; B.leaf = A.leaf; B.q = A.q; B.k = A.k; B.eta = A.eta;
+  B.fmt = A.fmt; B.with_f32 = false; B.apply_only = true;
+  B.L = A.L; B.KD = A.KD; B.KC = A.KC; B.tstar = A.tstar; B.lev_nat = A.lev_nat; B.lev = 1;
+  B.offsets = A.offsets; B.far = A.far; B.inadm = A.inadm; B.h_rank = A.h_rank;
+  B.d_perm = A.d_perm; B.d_slot_of = A.d_slot_of; B.d_leafoff = A.d_leafoff; B.d_X = A.d_X;
+  B.d_box = A.d_box; B.d_nodes = A.d_nodes; B.d_rank = A.d_rank;
+  B.d_U = A.d_U; B.d_E = A.d_E; B.d_R = A.d_R; B.d_UT = A.d_UT; B.d_ET = A.d_ET;
+  B.poolE = A.poolE;            // swizzled transfers (shared, not owned)
+  B.d_flag = (int*)B.alloc(sizeof(int) * 4);
+  B.d_sw = (double*)B.alloc(sizeof(double) * B.n);
+  B.d_dg = (double*)B.alloc(sizeof(double) * B.n);
+  { k_point_weights<<<ceil_div(B.n, 256), 256, 0, s>>>(B.d_perm, B.n, B.dim, B.d_X, nullptr, nullptr, B.kp,
+                                                       B.d_sw, B.d_dg); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
+  build_blocks(B, &A);
+  setup_operators(B);
+  H2_CUDA(cudaStreamSynchronize(s));
+}
+
 }  // namespace h2mg
 
 using namespace h2mg;
@@ -487,6 +510,41 @@ h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* m
     if (launches) *launches = (int64_t)P.used;
     if (ms) *ms = t;
     if (bytes) *bytes = by;
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_build_sibling(h2mg_matrix A, const h2mg_kernel* k, void* stream, h2mg_matrix* out) {
+  if (out) *out = nullptr;
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && k && out, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    H2_REQUIRE(k->kind >= 0 && k->kind <= H2MG_K_DMATERN32_DL && k->kind != H2MG_K_LAPLACE_SL,
+               H2MG_ERR_INVALID_ARG, "unsupported kernel for a sibling");
+    H2_REQUIRE(!k->weights && !k->diag, H2MG_ERR_INVALID_ARG, "siblings take no weights or diagonal");
+    H2_REQUIRE(k->kind == H2MG_K_POLY || (k->length > 0 && std::isfinite(k->length)), H2MG_ERR_INVALID_ARG,
+               "length must be > 0");
+    H2_REQUIRE(!A->M.has_weights && !A->M.has_diag, H2MG_ERR_INVALID_ARG,
+               "the base matrix has weights or a diagonal override");
+    auto* h = new h2mg_matrix_s();
+    h->M.stream = (cudaStream_t)stream;
+    h->M.kp = KernelParams{k->kind, k->length, k->nugget, k->degree};
+    try {
+      build_sibling(h->M, A->M, k);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return H2MG_OK;
+  });
+}
+
+h2mg_status h2mg_dot(const double* x, const double* y, int64_t n, double* out, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(x && y && out && n >= 0, H2MG_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevView X(x, n, true, s), Y(y, n, true, s);
+    *out = device_dot(X.d, Y.d, n, s);
     return H2MG_OK;
   });
 }

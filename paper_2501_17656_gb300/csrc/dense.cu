@@ -161,51 +161,116 @@ __global__ void k_syrk_update(double* __restrict__ A, int64_t n, int k0, int nb,
   }
 }
 
-// Forward step k0 of L y = w: every CTA solves the diagonal block from w[k0:k0+nb]
-// (which no CTA writes in this step); CTA 0 stores y_blk; each CTA then updates its
-// rows w[i], i >= k0 + nb.
-__global__ void k_trsv_fwd(const double* __restrict__ A, int64_t n, int k0, int nb,
-                           double* __restrict__ w, double* __restrict__ y) {
-  __shared__ double yb[NB];
-  if (threadIdx.x < nb) yb[threadIdx.x] = w[k0 + threadIdx.x];
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) yb[j] /= A[(k0 + j) + (int64_t)(k0 + j) * n];
-    __syncthreads();
-    if (threadIdx.x > j && threadIdx.x < nb) yb[threadIdx.x] -= A[(k0 + threadIdx.x) + (int64_t)(k0 + j) * n] * yb[j];
-    __syncthreads();
+// ----------------------------------------------------------------------------- inverse
+// A_l^{-1} from the Cholesky factor, by substitution on the identity, all columns at
+// once: L Y = I (forward, block row by block row), then L^T X = Y (backward). Each
+// step solves the NB x NB diagonal block for every column (one thread per column),
+// then updates the remaining rows with a 64 x 64-tiled product.
+__global__ void k_inv_diag(const double* __restrict__ L, int64_t n, int k0, int nb, int fwd,
+                           double* __restrict__ B) {
+  __shared__ double Lk[NB * NB];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int i = e % nb, j = e / nb;
+    Lk[e] = L[(k0 + i) + (int64_t)(k0 + j) * n];
   }
-  if (blockIdx.x == 0 && threadIdx.x < nb) y[k0 + threadIdx.x] = yb[threadIdx.x];
-  int64_t i = (int64_t)k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    double v = w[i];
-    for (int t = 0; t < nb; ++t) v -= A[i + (int64_t)(k0 + t) * n] * yb[t];
-    w[i] = v;
+  __syncthreads();
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double v[NB];
+  for (int i = 0; i < nb; ++i) v[i] = B[(k0 + i) + c * n];
+  if (fwd) {
+    for (int i = 0; i < nb; ++i) {
+      double t = v[i];
+      for (int j = 0; j < i; ++j) t -= Lk[i + j * nb] * v[j];
+      v[i] = t / Lk[i + i * nb];
+    }
+  } else {
+    for (int i = nb - 1; i >= 0; --i) {
+      double t = v[i];
+      for (int j = i + 1; j < nb; ++j) t -= Lk[j + i * nb] * v[j];
+      v[i] = t / Lk[i + i * nb];
+    }
+  }
+  for (int i = 0; i < nb; ++i) B[(k0 + i) + c * n] = v[i];
+}
+
+// fwd: B[i, c] -= sum_t L[i, k0+t] B[k0+t, c] for i >= k0+nb;
+// bwd: B[i, c] -= sum_t L[k0+t, i] B[k0+t, c] for i < k0.
+__global__ void k_inv_update(const double* __restrict__ L, int64_t n, int k0, int nb, int fwd, int row0,
+                             int rows, double* __restrict__ B) {
+  __shared__ double Lp[64 * NB], Bb[NB * 64];
+  int rt = blockIdx.x, ct = blockIdx.y;
+  int64_t r0 = row0 + (int64_t)rt * 64, c0 = (int64_t)ct * 64;
+  for (int e = threadIdx.x; e < 64 * nb; e += blockDim.x) {
+    int i = e % 64, t = e / 64;
+    int64_t r = r0 + i;
+    double v = 0.0;
+    if (r < row0 + rows) v = fwd ? L[r + (int64_t)(k0 + t) * n] : L[(k0 + t) + r * n];
+    Lp[e] = v;
+    int tt = e % nb, cc = e / nb;
+    Bb[e] = (c0 + cc < n) ? B[(k0 + tt) + (c0 + cc) * n] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    int i = e % 64, j = e / 64;
+    int64_t r = r0 + i, c = c0 + j;
+    if (r < row0 + rows && c < n) {
+      double s = 0.0;
+      for (int t = 0; t < nb; ++t) s += Lp[i + t * 64] * Bb[t + j * nb];
+      B[r + c * n] -= s;
+    }
   }
 }
 
-// Backward step k0 of L^T x = y: every CTA solves the diagonal block from y[k0:k0+nb];
-// CTA 0 stores x_blk; each CTA updates its rows y[i], i < k0 (one warp per row).
-__global__ void k_trsv_bwd(const double* __restrict__ A, int64_t n, int k0, int nb,
-                           double* __restrict__ y, double* __restrict__ x) {
-  __shared__ double xb[NB];
-  if (threadIdx.x < nb) xb[threadIdx.x] = y[k0 + threadIdx.x];
-  __syncthreads();
-  for (int j = nb - 1; j >= 0; --j) {
-    if (threadIdx.x == 0) xb[j] /= A[(k0 + j) + (int64_t)(k0 + j) * n];
-    __syncthreads();
-    if (threadIdx.x < j) xb[threadIdx.x] -= A[(k0 + j) + (int64_t)(k0 + threadIdx.x) * n] * xb[j];
-    __syncthreads();
+__global__ void k_identity(double* __restrict__ B, int64_t n) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n * n) B[e] = (e % n == e / n) ? 1.0 : 0.0;
+}
+
+// e[i] = sum_j Ainv[j, i] r[j]: one warp per output, reading column i (contiguous).
+__global__ void k_symv_cols(const double* __restrict__ Ainv, int64_t n, const double* __restrict__ r,
+                            double* __restrict__ e) {
+  int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const double* col = Ainv + i * n;
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s = fma(col[j], r[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) e[i] = s;
+}
+
+static void build_inverse(Matrix& M) {
+  cudaStream_t s = M.stream;
+  int64_t n = M.nl;
+  double* B = (double*)M.alloc(sizeof(double) * n * n);
+  { k_identity<<<ceil_div(n * n, 256), 256, 0, s>>>(B, n); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
+  int cgrid = ceil_div(n, 128);
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    int nb = (int)std::min<int64_t>(NB, n - k0);
+    { k_inv_diag<<<cgrid, 128, 0, s>>>(M.d_Al, n, k0, nb, 1, B); ::h2mg::count_launch(); }
+    H2_LAUNCH_CHECK();
+    int64_t rem = n - k0 - nb;
+    if (rem > 0) {
+      dim3 grid(ceil_div(rem, 64), ceil_div(n, 64));
+      { k_inv_update<<<grid, 256, 0, s>>>(M.d_Al, n, k0, nb, 1, k0 + nb, (int)rem, B); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x < nb) x[k0 + threadIdx.x] = xb[threadIdx.x];
-  int warps = blockDim.x / 32, lane = threadIdx.x & 31;
-  int64_t i = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
-  if (i < k0) {
-    double v = 0.0;
-    for (int t = lane; t < nb; t += 32) v += A[(k0 + t) + i * n] * xb[t];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) y[i] -= v;
+  int last = (int)((n - 1) / NB) * NB;
+  for (int k0 = last; k0 >= 0; k0 -= NB) {
+    int nb = (int)std::min<int64_t>(NB, n - k0);
+    { k_inv_diag<<<cgrid, 128, 0, s>>>(M.d_Al, n, k0, nb, 0, B); ::h2mg::count_launch(); }
+    H2_LAUNCH_CHECK();
+    if (k0 > 0) {
+      dim3 grid(ceil_div(k0, 64), ceil_div(n, 64));
+      { k_inv_update<<<grid, 256, 0, s>>>(M.d_Al, n, k0, nb, 0, 0, k0, B); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+    }
   }
+  H2_CUDA(cudaStreamSynchronize(s));
+  M.d_Ainv = B;
 }
 
 static void upload_i32(Matrix& M, const std::vector<int>& v, int** d) {
@@ -315,6 +380,7 @@ void build_dense_coarse(Matrix& M) {
   H2_CUDA(cudaMemcpyAsync(&flag, M.d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   H2_CUDA(cudaStreamSynchronize(s));
   M.coarse_ok = (flag == 0);
+  if (M.coarse_ok) build_inverse(M);
   M.wcoarse.bytes = sizeof(double) * 3 * (size_t)M.nl;
   M.wcoarse.p = M.alloc(M.wcoarse.bytes);
 }
@@ -330,36 +396,27 @@ __global__ void k_from_slots(const double* __restrict__ v, const int* __restrict
   if (i < n) out[i] = v[slot_of[i]];
 }
 
-// e = A_l^{-1} r with the Cholesky factor (workspace: three vectors of the coarse
-// size; r and e may alias). For l = 1 the vectors are in user point order and are
-// mapped to and from the padded point slots of the dense A_1.
+// e = A_l^{-1} r, with A_l^{-1} formed from the Cholesky factor at build time: one
+// warp per output reads one column of the (symmetric) inverse. For l = 1 the vectors
+// are in user point order and are mapped to and from the padded point slots.
 void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s) {
   int64_t n = M.nl;
   double* w = (double*)M.wcoarse.p;
-  double* y = w + n;
-  double* x = y + n;
+  double* x = w + n;
+  const double* rin = r;
+  double* eout = e;
   if (M.lev == 1) {
     H2_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * n, s));
     { k_to_slots<<<ceil_div(M.n, 256), 256, 0, s>>>(r, M.d_slot_of, M.n, w); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
-  } else {
+    rin = w;
+    eout = x;
+  } else if (r == e) {
     H2_CUDA(cudaMemcpyAsync(w, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    rin = w;
   }
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    int nb = (int)std::min<int64_t>(NB, n - k0);
-    int64_t rem = n - k0 - nb;
-    int grid = rem > 0 ? ceil_div(rem, 128) : 1;
-    { k_trsv_fwd<<<grid, 128, 0, s>>>(M.d_Al, n, k0, nb, w, y); ::h2mg::count_launch(); }
-    H2_LAUNCH_CHECK();
-  }
-  double* xo = (M.lev == 1) ? x : e;
-  int last = (int)((n - 1) / NB) * NB;
-  for (int k0 = last; k0 >= 0; k0 -= NB) {
-    int nb = (int)std::min<int64_t>(NB, n - k0);
-    int grid = k0 > 0 ? ceil_div(k0, 8) : 1;   // 8 warps per block
-    { k_trsv_bwd<<<grid, 256, 0, s>>>(M.d_Al, n, k0, nb, y, xo); ::h2mg::count_launch(); }
-    H2_LAUNCH_CHECK();
-  }
+  { k_symv_cols<<<ceil_div(n, 8), 256, 0, s>>>(M.d_Ainv, n, rin, eout); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
   if (M.lev == 1) {
     { k_from_slots<<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, e); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();

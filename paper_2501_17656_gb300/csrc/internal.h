@@ -19,8 +19,7 @@ struct DevBuf {
 // A symmetric block-sparse operator over one index space of "slots" (clusters),
 // stored as its upper triangle: row t holds entries (t, s) with s >= t. Each
 // entry points at a K x K block in some pool (swizzled layout, see swz). The
-// transposed product of entry (t, s), s > t, is written to the entry's scratch
-// row and gathered for row s by `gptr/gent`.
+// transposed product of entry (t, s), s > t, is added into output row s.
 struct SymOp {
   int K = 0;
   int nrows = 0;          // slots
@@ -29,9 +28,7 @@ struct SymOp {
   int* col = nullptr;     // [nnz]
   const void** blk = nullptr;      // [nnz] block pointers into the primary pool
   const void** blk32 = nullptr;    // [nnz] block pointers into the FP32 pool (or null)
-  int* gptr = nullptr;    // [nrows + 1] gather lists
-  int* gent = nullptr;    // entries e with col[e] == row and row(e) < col[e]
-  int64_t noff = 0;       // off-diagonal entries (each writes K transposed partials)
+  int64_t noff = 0;       // off-diagonal entries (each adds K transposed partials)
   int64_t bytes(int eb, int vb) const {   // algorithmic bytes of one product
     return (int64_t)nnz * K * K * eb + (int64_t)nrows * K * vb * 2 + noff * K * vb;
   }
@@ -97,6 +94,8 @@ struct Matrix {
 
   // ---- block pools (primary format and optional FP32 copy)
   DevBuf poolD, poolS, poolD32, poolS32;
+  DevBuf poolE, poolE32;                      // swizzled transfers, one per slot (levels > t*)
+                                              // (a sibling matrix shares its base's poolE)
   std::vector<DevBuf> poolP, poolP32;         // index = multigrid level i (2..lev)
   int64_t nD = 0, nS = 0;                     // stored blocks
   std::vector<int64_t> nP;
@@ -111,12 +110,12 @@ struct Matrix {
   // ---- dense coarsest operator and Cholesky factor
   int nl = 0;                   // size of A_l
   double* d_Al = nullptr;       // [nl * nl] column-major; lower triangle holds the factor
+  double* d_Ainv = nullptr;     // [nl * nl] A_l^{-1} formed from the factor
   bool coarse_ok = false;
 
   // ---- workspaces
   DevBuf wx, wyrow, wyc;        // coefficient buffers (nslots * KC elements, 8 B)
   DevBuf wxp, wyp;              // point buffers (2^L * KD elements, 8 B)
-  DevBuf wz;                    // scratch for transposed products
   DevBuf wstage;                // host staging
   DevBuf wvec;                  // multigrid vectors (float64)
   DevBuf wred;                  // reduction partials + scalars
@@ -143,11 +142,11 @@ void build_dense_coarse(Matrix& M);
 void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s);
 // ---- apply.cu
 struct ApplyWork {                // workspace of one product (see apply_impl)
-  void *xc, *yr, *yc, *xp, *yp, *z;
+  void *xc, *yr, *yc, *xp, *yp;
 };
 void setup_operators(Matrix& M);
 void apply_level1_ws(Matrix& M, const double* x, double* y, cudaStream_t s, const ApplyWork& ws);
-void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts, size_t* z);
+void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts);
 void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s);
 int64_t apply_bytes(const Matrix& M, int i);
 // ---- solve.cu
@@ -160,6 +159,7 @@ void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double*
 h2mg_status solve(Matrix& M, const double* b, double* x, const h2mg_solve_opts& o,
                   h2mg_solve_info* info, cudaStream_t s);
 int64_t level_size(const Matrix& M, int i);
+double device_dot(const double* a, const double* b, int64_t n, cudaStream_t s);
 
 // ---- sort.cu (device primitives)
 void exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, Matrix& M);

@@ -5,9 +5,9 @@
 // running while a stream is being captured into a CUDA graph, code inside an
 // allocator callback, or processes whose device memory is entirely reserved up front
 // by another allocator (a framework's caching pool). This entry point allocates
-// nothing: the product's workspace (coefficient buffers, point buffers and the
-// scratch rows of the transposed block products) lives in the file-scope array
-// below, whose address is looked up once per device.
+// nothing: the product's workspace (coefficient buffers, point buffers and the row
+// accumulators of the block products) lives in the file-scope array below, whose
+// address is looked up once per device.
 #include <mutex>
 #include <string>
 
@@ -53,9 +53,9 @@ extern "C" h2mg_status h2mg_apply_noalloc(h2mg_matrix A, const double* x, double
     H2_REQUIRE(is_device_pointer(x) && is_device_pointer(y), H2MG_ERR_INVALID_ARG,
                "h2mg_apply_noalloc needs device vectors (host vectors would need staging memory)");
     Matrix& M = A->M;
-    size_t coef, pts, z;
-    apply_level1_ws_sizes(M, &coef, &pts, &z);
-    size_t need = 3 * up256(coef) + 2 * up256(pts) + up256(z);
+    size_t coef, pts;
+    apply_level1_ws_sizes(M, &coef, &pts);
+    size_t need = 3 * up256(coef) + 2 * up256(pts);
     if (need > (size_t)H2MG_NOALLOC_SCRATCH_BYTES)
       throw Error{H2MG_ERR_UNSUPPORTED, "this matrix needs " + std::to_string(need) +
                                             " bytes of scratch; the fixed array holds " +
@@ -68,8 +68,7 @@ extern "C" h2mg_status h2mg_apply_noalloc(h2mg_matrix A, const double* x, double
     ws.yr = p; p += up256(coef);
     ws.yc = p; p += up256(coef);
     ws.xp = p; p += up256(pts);
-    ws.yp = p; p += up256(pts);
-    ws.z = p;
+    ws.yp = p;
     // padded point slots are read as zeros by the block product; earlier calls may
     // have left other values there
     H2_CUDA(cudaMemsetAsync(ws.xp, 0, pts, s));

@@ -13,7 +13,8 @@ namespace h2mg {
 // ----------------------------------------------------------------------------- reductions
 constexpr int NPART = 256;
 struct CGState {
-  double rho, alpha, beta, thresh;
+  double rho[2];   // r^T r, double-buffered by iteration parity
+  double thresh;
   int stopped;
 };
 
@@ -53,25 +54,38 @@ __global__ void k_cg_init(const double* __restrict__ prr, int nrr, const double*
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double rr = sum_parts(prr, nrr), ff = sum_parts(pff, nff);
     double t = 1e-30 * sqrt(ff);
-    st->rho = rr;
+    st->rho[0] = rr;
     st->thresh = t * t;
     st->stopped = 0;
   }
 }
-__global__ void k_cg_alpha(const double* __restrict__ ppq, int np, CGState* st) {
-  if (threadIdx.x == 0 && blockIdx.x == 0 && !st->stopped) {
-    double pq = sum_parts(ppq, np);
-    if (!(pq > 0.0))
-      st->stopped = 1;
-    else
-      st->alpha = st->rho / pq;
-  }
+
+// Sum of np (<= 256) partials, by every CTA (blockDim 256).
+__device__ double cta_sum_parts(const double* __restrict__ part, int np) {
+  __shared__ double sh[8];
+  double v = threadIdx.x < np ? part[threadIdx.x] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < 8; ++i) s += sh[i];
+  __syncthreads();
+  return s;
 }
-__global__ void k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                            const double* __restrict__ q, int64_t n, const CGState* st,
-                            double* __restrict__ part) {
-  const bool go = !st->stopped;
-  const double al = st->alpha;
+
+// alpha = rho / p^T q (stop before the update if p^T q <= 0); x += alpha p;
+// r -= alpha q; partials of r^T r. Every CTA takes the same decision.
+__global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ x, double* __restrict__ r,
+                                                   const double* __restrict__ p, const double* __restrict__ q,
+                                                   int64_t n, CGState* st, const double* __restrict__ ppq, int np,
+                                                   int par, double* __restrict__ part) {
+  const double pq = cta_sum_parts(ppq, np);
+  bool go = !st->stopped;
+  if (go && !(pq > 0.0)) {
+    go = false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->stopped = 1;
+  }
+  const double al = go ? st->rho[par] / pq : 0.0;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double ri = r[i];
@@ -85,20 +99,18 @@ __global__ void k_cg_update(double* __restrict__ x, double* __restrict__ r, cons
   s = block_reduce_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
-__global__ void k_cg_beta(const double* __restrict__ prr, int np, CGState* st) {
-  if (threadIdx.x == 0 && blockIdx.x == 0 && !st->stopped) {
-    double rn = sum_parts(prr, np);
-    if (rn <= st->thresh) {
-      st->stopped = 1;
-    } else {
-      st->beta = rn / st->rho;
-      st->rho = rn;
-    }
-  }
-}
-__global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ r, int64_t n, const CGState* st) {
+
+// rho' = r^T r; stop (after the update) if rho' <= thresh; else p = r + (rho'/rho) p.
+__global__ void __launch_bounds__(256) k_cg_p(double* __restrict__ p, const double* __restrict__ r, int64_t n,
+                                              CGState* st, const double* __restrict__ prr, int np, int par) {
+  const double rn = cta_sum_parts(prr, np);
   if (st->stopped) return;
-  const double be = st->beta;
+  if (rn <= st->thresh) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->stopped = 1;
+    return;
+  }
+  const double be = rn / st->rho[par];
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->rho[par ^ 1] = rn;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = fma(be, p[i], r[i]);
 }
@@ -260,12 +272,12 @@ void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n
   { k_cg_init<<<1, 32, 0, s>>>(W.pa, part_grid(N), W.pb, part_grid(N), W.st); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   for (int it = 0; it < n; ++it) {
+    const int par = it & 1;
     apply_level(M, i, f32, W.cp, W.cq, s);
     dot_part(W.cp, W.cq, N, W.pa, s);
-    { k_cg_alpha<<<1, 32, 0, s>>>(W.pa, part_grid(N), W.st); ::h2mg::count_launch(); }
-    { k_cg_update<<<part_grid(N), 256, 0, s>>>(x, rr, W.cp, W.cq, N, W.st, W.pb); ::h2mg::count_launch(); }
-    { k_cg_beta<<<1, 32, 0, s>>>(W.pb, part_grid(N), W.st); ::h2mg::count_launch(); }
-    { k_cg_p<<<g, 256, 0, s>>>(W.cp, rr, N, W.st); ::h2mg::count_launch(); }
+    { k_cg_update<<<part_grid(N), 256, 0, s>>>(x, rr, W.cp, W.cq, N, W.st, W.pa, part_grid(N), par, W.pb); ::h2mg::count_launch(); }
+    H2_LAUNCH_CHECK();
+    { k_cg_p<<<g, 256, 0, s>>>(W.cp, rr, N, W.st, W.pb, part_grid(N), par); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
 }
@@ -343,6 +355,26 @@ static double norm2(Matrix& M, const double* v, int64_t n, cudaStream_t s) {
   double t = 0.0;
   for (double x : h) t += x;
   return std::sqrt(t);
+}
+
+// x^T y on the device (two-pass deterministic sum), read back to the host.
+double device_dot(const double* a, const double* b, int64_t n, cudaStream_t s) {
+  if (n == 0) return 0.0;
+  double* part = nullptr;
+  H2_CUDA(cudaMalloc(&part, sizeof(double) * NPART));
+  double t = 0.0;
+  try {
+    dot_part(a, b, n, part, s);
+    std::vector<double> h(part_grid(n));
+    H2_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    for (double v : h) t += v;
+  } catch (...) {
+    cudaFree(part);
+    throw;
+  }
+  cudaFree(part);
+  return t;
 }
 
 static double dot_host(Matrix& M, const double* a, const double* b, int64_t n, cudaStream_t s) {

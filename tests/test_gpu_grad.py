@@ -1,0 +1,100 @@
+"""GPU adjoint gradients (the differentiation form) against the oracle, central
+differences and dense float64 autograd, on the Matern-3/2 workload at 2^12 points."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.grad import derivative_h2, matern_grads
+from oracle.h2 import H2Matrix, KernelSpec
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2501_17656_gb300 as pkg  # noqa: E402
+
+N, L_, S_ = 4096, 0.1, 1e-2
+
+
+@pytest.fixture(scope="module")
+def data():
+    X = W.uniform_points(N, 3, 4)
+    rng = np.random.default_rng(2004)
+    return X, rng.standard_normal(N), rng.standard_normal(N)
+
+
+def cuda(a, grad=False):
+    return torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=grad)
+
+
+def gpu_loss_grads(X, y, b, l, s, tol=1e-12):
+    yt, bt = cuda(y, True), cuda(b, True)
+    lt, st = cuda(l, True), cuda(s, True)
+    L = pkg.MaternLoss.apply(torch.from_numpy(X).cuda(), yt, bt, lt, st, tol=tol)
+    L.backward()
+    return L.item(), yt.grad.cpu().numpy(), bt.grad.cpu().numpy(), lt.grad.item(), st.grad.item()
+
+
+def test_derivative_sibling_matches_oracle(data):
+    X, _, _ = data
+    A = pkg.H2Matrix(torch.from_numpy(X).cuda(), "matern32", length=L_, nugget=S_, leaf=64, q=4)
+    dA = A.sibling("dmatern32_dl", length=L_)
+    h = H2Matrix(X, KernelSpec("matern32", L_, S_), 64, 4, 1.0)
+    dh = derivative_h2(h, KernelSpec("dmatern32_dl", L_, 0.0))
+    v = np.random.default_rng(3).standard_normal(N)
+    got = dA.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    ref = dh.apply(v)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    with pytest.raises(pkg.H2MGError):
+        dA.solve(torch.from_numpy(v).cuda())
+    dA.close()
+    A.close()
+
+
+def test_adjoint_gradients_match_oracle(data):
+    X, y, b = data
+    L, gy, gb, gl, gs = gpu_loss_grads(X, y, b, L_, S_)
+    Lo, a, w, dl, ds = matern_grads(X, y, b, L_, S_, leaf=64, q=4)
+    assert abs(L - Lo) <= 1e-9 * abs(Lo)
+    assert np.linalg.norm(gy - a) <= 1e-8 * np.linalg.norm(a)
+    assert np.linalg.norm(gb - w) <= 1e-8 * np.linalg.norm(w)
+    assert abs(gl - dl) <= 1e-8 * abs(dl)
+    assert abs(gs - ds) <= 1e-8 * abs(ds)
+
+
+def test_adjoint_gradients_match_central_differences(data):
+    X, y, b = data
+    _, _, _, gl, gs = gpu_loss_grads(X, y, b, L_, S_, tol=1e-13)
+
+    def loss(l, s):
+        with torch.no_grad():
+            return pkg.MaternLoss.apply(torch.from_numpy(X).cuda(), cuda(y), cuda(b), cuda(l), cuda(s),
+                                        tol=1e-13).item()
+
+    h = 1e-4
+    fd_l = (loss(L_ * (1 + h), S_) - loss(L_ * (1 - h), S_)) / (2 * h * L_)
+    fd_s = (loss(L_, S_ * (1 + h)) - loss(L_, S_ * (1 - h))) / (2 * h * S_)
+    assert abs(gl - fd_l) <= 1e-6 * abs(fd_l), (gl, fd_l)
+    assert abs(gs - fd_s) <= 1e-6 * abs(fd_s), (gs, fd_s)
+
+
+def test_adjoint_gradients_near_dense_autograd(data):
+    """Against the exact (dense) kernel the difference is the H2 compression error of
+    the 4x4x4-node interpolation, not an error of the adjoint."""
+    X, y, b = data
+    L, gy, gb, gl, gs = gpu_loss_grads(X, y, b, L_, S_)
+    Xt = torch.tensor(X, dtype=torch.float64, device="cuda")
+    lt, st = cuda(L_, True), cuda(S_, True)
+    yt, bt = cuda(y, True), cuda(b, True)
+    u = math.sqrt(3.0) * torch.cdist(Xt, Xt) / lt
+    K = (1 + u) * torch.exp(-u) + st * torch.eye(N, dtype=torch.float64, device="cuda")
+    Lt = 0.5 * yt @ torch.linalg.solve(K, yt) + torch.linalg.solve(K, bt).sum()
+    Lt.backward()
+    assert abs(L - Lt.item()) <= 1e-3 * abs(Lt.item())
+    assert abs(gl - lt.grad.item()) <= 1e-2 * abs(lt.grad.item())
+    assert abs(gs - st.grad.item()) <= 1e-2 * abs(st.grad.item())
+    assert np.linalg.norm(gb - bt.grad.cpu().numpy()) <= 1e-2 * np.linalg.norm(gb)

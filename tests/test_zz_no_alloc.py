@@ -58,9 +58,10 @@ def test_noalloc_rejects_host_vectors_and_oversized_problems():
         A.apply_noalloc(xh, np.empty_like(xh))
     assert e.value.name == "INVALID_ARG"
     A.close()
-    X = torch.from_numpy(W.uniform_points(1 << 17, 3, 2)).cuda()
-    B = pkg.H2Matrix(X, "gaussian", length=0.05, nugget=1e-3, leaf=64, q=4, eta=1.0)
-    x = torch.ones(1 << 17, dtype=torch.float64, device="cuda")
+    n = 1 << 19   # about 64 bytes of workspace per point: above the fixed 16 MiB
+    X = torch.from_numpy(W.uniform_points(n, 2, 2)).cuda()
+    B = pkg.H2Matrix(X, "exponential", length=0.1, nugget=1e-2, leaf=32, q=3, eta=1.0)
+    x = torch.ones(n, dtype=torch.float64, device="cuda")
     with pytest.raises(pkg.H2MGError) as e:
         B.apply_noalloc(x, torch.empty_like(x))
     assert e.value.name == "UNSUPPORTED"
