@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=8192)
     ap.add_argument("--no-f64", action="store_true", help="skip the plain float64 comparison solve")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph V-cycle measurement")
+    ap.add_argument("--batch-rhs", type=int, default=4,
+                    help="right-hand sides of the batched solve measured after the timed region (0: skip)")
     return ap.parse_args()
 
 
@@ -318,6 +321,39 @@ def main():
         f64 = {"s_per_solve": s64, "solves_per_s": 1.0 / s64, "cycles": i64.cycles,
                "converged": bool(i64.converged), "relres": i64.relres,
                "mixed_speedup": s64 / (ms / 1e3 / a.steps)}
+    # ---- the same solve with the V-cycle replayed from a captured CUDA graph, timed once
+    graph = None
+    if not a.no_graph:
+        A.solve(b, raise_on_fail=False, use_graph=True, **kw)      # capture
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        xg_, ig_ = A.solve(b, raise_on_fail=False, use_graph=True, **kw)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        sg = h0.elapsed_time(h1) / 1e3
+        graph = {"s_per_solve": sg, "solves_per_s": 1.0 / sg, "cycles": ig_.cycles,
+                 "converged": bool(ig_.converged), "speedup_vs_direct": (ms / 1e3 / a.steps) / sg}
+
+    # ---- batched form: several right-hand sides solved together (one group of columns
+    # shares every block read of every product), timed once
+    batched = None
+    if a.batch_rhs > 0:
+        Bm = torch.from_numpy(np.ascontiguousarray(W.normal_rhs(a.n, 2, a.batch_rhs))).cuda() \
+            if a.batch_rhs > 1 else b[:, None].clone()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        Xb, ib = A.solve(Bm, raise_on_fail=False, **kw)
+        ib = ib if isinstance(ib, list) else [ib]
+        g1.record(stream)
+        torch.cuda.synchronize()
+        sb = g0.elapsed_time(g1) / 1e3
+        Rb = Bm - A.apply(Xb)
+        relb = (Rb.norm(dim=0) / Bm.norm(dim=0)).max().item()
+        batched = {"nrhs": a.batch_rhs, "s_per_batch": sb, "solves_per_s": a.batch_rhs / sb,
+                   "max_relres": relb, "converged": bool(relb <= a.tol * 1.0001) and all(i.converged for i in ib),
+                   "cycles": [i.cycles for i in ib],
+                   "speedup_vs_single_rhs": (a.batch_rhs / sb) / (a.steps / (ms / 1e3)),
+                   "precision": a.precision}
     A.close()
 
     kernel_gbs = kby / kms / 1e6 if kms > 0 else 0.0
@@ -340,7 +376,7 @@ def main():
                        "l2": "inputs larger than L2 (stored blocks)", "build_s": build_s,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "cycles": cycles, "converged": converged, "relres": infos[-1][2], "relres_check": res_check,
-            "matvec": matvec, "f64_solve": f64, "roofline": roof, "gpu_launches": launches,
+            "matvec": matvec, "f64_solve": f64, "graph": graph, "batched": batched, "roofline": roof, "gpu_launches": launches,
             "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 16 * a.n,
                     "d2h_bytes_per_step": 8 * a.n},
             "clocks": clk.summary()}

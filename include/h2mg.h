@@ -98,7 +98,14 @@ typedef struct {
                                        0: use CG's recurrence residual (equal in exact arithmetic) */
     int outer;                      /* h2mg_outer: repeated V-cycles (Sec. 3.3) or flexible CG
                                        preconditioned by one V-cycle */
-    int use_graph;                  /* 1: capture one V-cycle as a CUDA graph and replay it */
+    int use_graph;                  /* 1: capture the V-cycle (smoothers, transfers, coarse
+                                       solve: no host synchronisation inside) as a CUDA graph
+                                       on the first solve with these settings and column
+                                       count, then replay it with one launch per outer
+                                       iteration; the graph is kept with the matrix.
+                                       While h2mg_profile is enabled the V-cycle is
+                                       launched directly (profiling events are recorded
+                                       from the host around each block product) */
 } h2mg_solve_opts;
 
 typedef struct {
@@ -121,16 +128,22 @@ h2mg_status h2mg_build(const double* points, int64_t n, int dim, const h2mg_kern
 
 /* y = A x (Sec. 3.1, the H2 matrix-vector product x_i = V_i x_{i-1},
  * y_{i-1} = D_i x_{i-1} + U_i y_i). nrhs >= 1 columns, leading dimension ld >= n.
- * x and y must not overlap. Uses the primary storage copy. */
+ * x and y must not overlap. Uses the primary storage copy. Columns are taken in
+ * groups of up to four: each stored block is read once per group (two columns at a
+ * time go through one block product in float64 / double-float storage). */
 h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int64_t ld,
                        void* stream);
 
 /* Solve A x = b with H2-MG (Algorithm 1, repeated V-cycles, Sec. 3.3). On entry
  * x holds the initial guess x_0 (zeros are the paper's choice), on exit the
- * solution. nrhs >= 1 columns (each solved independently), leading dimension ld.
- * info (optional) receives the last column's statistics. Returns NOT_CONVERGED
- * (with x and info filled) if max_cycles is reached, NAN if b or a residual is not
- * finite. */
+ * solution. nrhs >= 1 columns, leading dimension ld. Columns are solved in groups
+ * of up to four that share every product, smoother step and V-cycle launch; each
+ * column has its own CG scalars, outer-loop coefficients and stopping test (a
+ * column that has converged keeps its x while the rest of its group runs on).
+ * info (optional) points to nrhs structs that receive each column's statistics
+ * (relres_hist and ms_solve are those of the column's group). Returns NOT_CONVERGED
+ * (with x and info filled) if max_cycles is reached for some column, NAN if b or a
+ * residual is not finite. */
 h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int64_t ld,
                        const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream);
 

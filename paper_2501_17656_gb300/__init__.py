@@ -156,6 +156,39 @@ def _like(x, n):
     return torch.zeros(n, dtype=torch.float64, device=x.device)
 
 
+def _colmajor(a):
+    """(buffer, nrhs): a 1-D vector, or a 2-D (n, nrhs) array / tensor as a
+    column-major buffer (the library's layout: column c at offset c * n). The buffer is
+    ``a``'s own memory when ``a`` is already column-major, else a packed copy."""
+    if len(a.shape) == 1:
+        return a, 1
+    if isinstance(a, np.ndarray):
+        return np.asfortranarray(a), int(a.shape[1])
+    t = a.t()
+    return (t if t.is_contiguous() else t.contiguous()), int(a.shape[1])
+
+
+def _new_cols(like, n, nrhs):
+    """A zeroed column-major (n, nrhs) buffer beside ``like`` (1-D when nrhs is None)."""
+    if nrhs is None:
+        return _like(like, n)
+    if isinstance(like, np.ndarray):
+        return np.zeros((n, nrhs), dtype=np.float64, order="F")
+    import torch
+    return torch.zeros((nrhs, n), dtype=torch.float64, device=like.device).t()
+
+
+def _copy_back(dst, buf):
+    """Write a packed column-major result into ``dst`` when ``buf`` is not its memory."""
+    if len(dst.shape) == 1:
+        return
+    if isinstance(dst, np.ndarray):
+        if buf is not dst:
+            dst[...] = buf
+    elif buf.data_ptr() != dst.data_ptr():
+        dst.copy_(buf.t())
+
+
 def dot(x, y) -> float:
     """x^T y (float64) reduced by the library on the GPU."""
     out = ctypes.c_double()
@@ -245,13 +278,14 @@ class H2Matrix:
 
     # ----------------------------------------------------------------- products
     def apply(self, x, y=None):
-        """y = A x (one or several columns; column-major for NumPy 2-D input)."""
-        if y is None:
-            y = x.clone() if not isinstance(x, np.ndarray) else np.empty_like(x)
-        nrhs = 1 if len(x.shape) == 1 else int(x.shape[1])
-        ld = self.n
-        _check(self._lib.h2mg_apply(self._h, _ptr(x), _ptr(y), nrhs, ld, _stream()))
-        return y
+        """y = A x for a vector or an (n, nrhs) block of columns; the columns go through
+        the products together, each stored block read once per group of four."""
+        xb, nrhs = _colmajor(x)
+        out = y if y is not None else _new_cols(x, self.n, None if len(x.shape) == 1 else nrhs)
+        yb, _ = _colmajor(out)
+        _check(self._lib.h2mg_apply(self._h, _ptr(xb), _ptr(yb), nrhs, self.n, _stream()))
+        _copy_back(out, yb)
+        return out
 
     def apply_noalloc(self, x, y):
         """y = A x without any device allocation (device tensors only; scratch in a
@@ -303,17 +337,20 @@ class H2Matrix:
         return x
 
     def solve(self, b, x=None, raise_on_fail: bool = True, **kw):
-        """Solve A x = b by H2-MG (Algorithm 1 repeated). Returns (x, SolveInfo)."""
+        """Solve A x = b by H2-MG (Algorithm 1 repeated) for a vector or an (n, nrhs)
+        block of columns, solved together in groups of four. Returns (x, info): one
+        SolveInfo for a vector, a list with one per column for a block."""
+        bb, nrhs = _colmajor(b)
         if x is None:
-            x = _like(b, b.shape if len(b.shape) > 1 else self.n)
-        nrhs = 1 if len(b.shape) == 1 else int(b.shape[1])
+            x = _new_cols(b, self.n, None if len(b.shape) == 1 else nrhs)
+        xb, _ = _colmajor(x)
         o = self._opts(**kw)
-        info = SolveInfo()
-        st = self._lib.h2mg_solve(self._h, _ptr(b), _ptr(x), nrhs, self.n, ctypes.byref(o), ctypes.byref(info),
-                                  _stream())
+        infos = (SolveInfo * nrhs)()
+        st = self._lib.h2mg_solve(self._h, _ptr(bb), _ptr(xb), nrhs, self.n, ctypes.byref(o), infos, _stream())
+        _copy_back(x, xb)
         if st != 0 and (raise_on_fail or st not in (5,)):
             _check(st)
-        return x, info
+        return x, (infos[0] if len(b.shape) == 1 else list(infos))
 
 
 # --------------------------------------------------------------------------- adjoint
@@ -323,7 +360,10 @@ class MaternLoss:
     adjoint method: dL/dy = K^{-1} y, dL/db = K^{-1} 1 (one extra H2-MG solve, K being
     symmetric), dL/dtheta = -1/2 a^T (dK/dtheta) a - w^T (dK/dtheta) x with a = K^{-1} y,
     x = K^{-1} b, w = K^{-1} 1; dK/dl is the H2 sibling of K with the derivative kernel
-    and dK/ds = I. Only the solution vectors are kept between forward and backward."""
+    and dK/ds = I. The forward pass solves for y, b and (when a gradient is wanted) the
+    ones vector together as one three-column H2-MG solve; the backward pass applies
+    dK/dl to a and x as one two-column product. Only the solution vectors are kept
+    between forward and backward."""
 
     @staticmethod
     def apply(points, y, b, length, nugget, leaf=64, q=4, eta=1.0, tol=1e-12, max_cycles=200,
@@ -335,22 +375,25 @@ class MaternLoss:
             def forward(ctx, y_, b_, l_, s_):
                 K = H2Matrix(points, "matern32", length=float(l_), nugget=float(s_), leaf=leaf, q=q, eta=eta)
                 kw = dict(tol=tol, max_cycles=max_cycles, outer=outer, n_f=n_f, n_c=n_c)
-                a, _ = K.solve(y_.detach().contiguous(), **kw)
-                x, _ = K.solve(b_.detach().contiguous(), **kw)
-                ones = torch.ones_like(x)
-                loss = 0.5 * dot(y_.detach().contiguous(), a) + dot(x, ones)
-                ctx.K, ctx.kw, ctx.l = K, kw, float(l_)
-                ctx.save_for_backward(a, x)
+                yd = y_.detach().contiguous()
+                ones = torch.ones_like(yd)
+                cols = [yd, b_.detach(), ones] if any(ctx.needs_input_grad) else [yd, b_.detach()]
+                B = torch.stack(cols).t()                       # (n, 2 or 3), column-major
+                S, _ = K.solve(B, **kw)
+                a, x = S[:, 0].contiguous(), S[:, 1].contiguous()
+                loss = 0.5 * dot(yd, a) + dot(x, ones)
+                ctx.K, ctx.l = K, float(l_)
+                w = S[:, 2].contiguous() if len(cols) == 3 else torch.empty(0, dtype=a.dtype, device=a.device)
+                ctx.save_for_backward(a, x, w)
                 return torch.tensor(loss, dtype=torch.float64, device=y_.device)
 
             @staticmethod
             def backward(ctx, g):
-                a, x = ctx.saved_tensors
+                a, x, w = ctx.saved_tensors
                 K = ctx.K
-                ones = torch.ones_like(x)
-                w, _ = K.solve(ones, **ctx.kw)
                 dK = K.sibling("dmatern32_dl", length=ctx.l)
-                dKa, dKx = dK.apply(a), dK.apply(x)
+                P = dK.apply(torch.stack([a, x]).t())
+                dKa, dKx = P[:, 0].contiguous(), P[:, 1].contiguous()
                 dl = -0.5 * dot(a, dKa) - dot(w, dKx)
                 ds = -0.5 * dot(a, a) - dot(w, x)
                 dK.close()

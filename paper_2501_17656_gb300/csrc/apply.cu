@@ -113,7 +113,9 @@ struct Ar<FMT_F32> {
 // copies, FP32 for the F32 copy) into a row buffer zeroed before the launch, so the
 // summation order, and the last bits of a sum, may differ from run to run. When the
 // operator has few rows, each row is split over `split` CTAs (strided entries).
-template <int K, int FMT>
+// NR right-hand sides share every block read: vectors are interleaved, element
+// (slot, coefficient, column j) at ((slot * K + coefficient) * NR + j).
+template <int K, int FMT, int NR>
 __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
                                                 const int* __restrict__ col,
                                                 const void* const* __restrict__ blk,
@@ -127,25 +129,29 @@ __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
   constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
   constexpr int CH = T < LPC ? T : LPC;
   constexpr int V = A::V, P = 8 / V;
-  __shared__ acc_t red[8][K];
+  __shared__ acc_t red[8][K * NR];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int row = blockIdx.x / split, part = blockIdx.x % split;
   const int rb = 8 * (lane % LPC), cl = lane / LPC;
-  vec_t xt[8];
+  vec_t xt[8][NR];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) xt[r] = x[(int64_t)row * K + rb + r];
-  acc_t ya[8];
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
-  for (int r = 0; r < 8; ++r) ya[r] = A::zero();
+    for (int j = 0; j < NR; ++j) xt[r][j] = x[((int64_t)row * K + rb + r) * NR + j];
+  acc_t ya[8][NR];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) ya[r][j] = A::zero();
   const int e0 = rowptr[row], e1 = rowptr[row + 1];
   for (int e = e0 + part * 8 + w; e < e1; e += 8 * split) {
     const int s = col[e];
     const ld_t* B = (const ld_t*)blk[e];
-    const vec_t* xs = x + (int64_t)s * K;
+    const vec_t* xs = x + (int64_t)s * K * NR;
     const bool off = (s != row);
 #pragma unroll 1
     for (int ch = 0; ch < T / CH; ++ch) {
-      acc_t zc[CH];
+      acc_t zc[CH][NR];
 #pragma unroll
       for (int tt = 0; tt < CH; ++tt) {
         const int t = ch * CH + tt;
@@ -155,92 +161,119 @@ __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
           ld_t v = __ldcs(B + (t * P + k) * 32 + lane);
           A::decode(v, m + k * V);
         }
-        const vec_t xv = xs[cl + CPP * t];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) A::fma(ya[r], m[r], xv);
-        acc_t zz = A::zero();
+        for (int j = 0; j < NR; ++j) {
+          const vec_t xv = xs[(cl + CPP * t) * NR + j];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r]);
-        zc[tt] = zz;
+          for (int r = 0; r < 8; ++r) A::fma(ya[r][j], m[r], xv);
+          acc_t zz = A::zero();
+#pragma unroll
+          for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r][j]);
+          zc[tt][j] = zz;
+        }
         if ((t & 3) == 3) {
 #pragma unroll
-          for (int r = 0; r < 8; ++r) A::norm(ya[r]);
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int j = 0; j < NR; ++j) A::norm(ya[r][j]);
         }
       }
       if (off) {
         // reduce the CH partial columns over the LPC lanes that share them
-        if (CH == LPC) {
 #pragma unroll
-          for (int h = CH / 2; h >= 1; h >>= 1) {
-            const bool up = (lane & h) != 0;
+        for (int j = 0; j < NR; ++j) {
+          if (CH == LPC) {
 #pragma unroll
-            for (int j = 0; j < h; ++j) {
-              acc_t send = up ? zc[j] : zc[j + h];
-              acc_t keep = up ? zc[j + h] : zc[j];
-              acc_t recv = A::shfl(send, h);
-              A::add(keep, recv);
-              zc[j] = keep;
+            for (int h = CH / 2; h >= 1; h >>= 1) {
+              const bool up = (lane & h) != 0;
+#pragma unroll
+              for (int q = 0; q < h; ++q) {
+                acc_t send = up ? zc[q][j] : zc[q + h][j];
+                acc_t keep = up ? zc[q + h][j] : zc[q][j];
+                A::add(keep, A::shfl(send, h));
+                zc[q][j] = keep;
+              }
             }
-          }
-          const int tt = lane & (CH - 1);
-          atomicAdd(yrow + (int64_t)s * K + cl + CPP * (ch * CH + tt), A::to_yo(A::out(zc[0])));
-        } else {
+            const int tt = lane & (CH - 1);
+            atomicAdd(yrow + ((int64_t)s * K + cl + CPP * (ch * CH + tt)) * NR + j, A::to_yo(A::out(zc[0][j])));
+          } else {
 #pragma unroll
-          for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0], A::shfl(zc[0], h));
-          if ((lane % LPC) == 0) atomicAdd(yrow + (int64_t)s * K + cl + CPP * (ch * CH), A::to_yo(A::out(zc[0])));
+            for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0][j], A::shfl(zc[0][j], h));
+            if ((lane % LPC) == 0)
+              atomicAdd(yrow + ((int64_t)s * K + cl + CPP * (ch * CH)) * NR + j, A::to_yo(A::out(zc[0][j])));
+          }
         }
       }
     }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) A::norm(ya[r]);
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) A::norm(ya[r][j]);
   }
   // rows: sum over the lanes that share them, then over the warps
 #pragma unroll
   for (int h = LPC; h < 32; h <<= 1)
 #pragma unroll
-    for (int r = 0; r < 8; ++r) A::add(ya[r], A::shfl(ya[r], h));
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) A::add(ya[r][j], A::shfl(ya[r][j], h));
   if (lane < LPC)
 #pragma unroll
-    for (int r = 0; r < 8; ++r) red[w][rb + r] = ya[r];
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) red[w][(rb + r) * NR + j] = ya[r][j];
   __syncthreads();
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+  for (int i = threadIdx.x; i < K * NR; i += blockDim.x) {
     acc_t s = red[0][i];
 #pragma unroll
     for (int ww = 1; ww < 8; ++ww) A::add(s, red[ww][i]);
-    atomicAdd(yrow + (int64_t)row * K + i, A::to_yo(A::out(s)));
+    atomicAdd(yrow + (int64_t)row * K * NR + i, A::to_yo(A::out(s)));
   }
 }
 
 // ----------------------------------------------------------------------------- passes
-// point vector (float64, user order) -> padded tree slots in the product format
-template <int FMT>
-__global__ void k_pts_in(const double* __restrict__ x, const int* __restrict__ slot_of, int64_t n,
+// point vectors (float64, user order, column j at x + j*ldx) -> padded tree slots
+template <int FMT, int NR>
+__global__ void k_pts_in(const double* __restrict__ x, int64_t ldx, const int* __restrict__ slot_of, int64_t n,
                          typename Ar<FMT>::vec_t* __restrict__ xp) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) xp[slot_of[i]] = Ar<FMT>::from_d(x[i]);
+  if (i >= n) return;
+  const int64_t sl = slot_of[i];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) xp[sl * NR + j] = Ar<FMT>::from_d(x[i + j * ldx]);
 }
 
-// coefficient vector (float64, KC per cluster) -> product format
-template <int FMT>
-__global__ void k_coef_in(const double* __restrict__ x, int64_t n, typename Ar<FMT>::vec_t* __restrict__ xc) {
+// coefficient vectors (float64, KC per cluster, column j at x + j*ldx) -> interleaved
+template <int FMT, int NR>
+__global__ void k_coef_in(const double* __restrict__ x, int64_t ldx, int64_t n,
+                          typename Ar<FMT>::vec_t* __restrict__ xc) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) xc[i] = Ar<FMT>::from_d(x[i]);
+  if (i >= n) return;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) xc[i * NR + j] = Ar<FMT>::from_d(x[i + j * ldx]);
 }
 
-// x_hat(leaf j)[b] = sum_i U_j[i, b] x_j[i]   (UT = U^T, KC x KD column-major)
-template <int FMT, class BT>
+// x_hat(leaf l)[b] = sum_i U_l[i, b] x_l[i]   (UT = U^T, KC x KD column-major)
+template <int FMT, class BT, int NR>
 __global__ void k_up_leaf(const BT* __restrict__ UT, int KD, int KC,
                           const typename Ar<FMT>::vec_t* __restrict__ xp,
                           typename Ar<FMT>::vec_t* __restrict__ xc) {
-  __shared__ double xs[64];
-  int j = blockIdx.x;
-  for (int i = threadIdx.x; i < KD; i += blockDim.x) xs[i] = Ar<FMT>::to_d(xp[(int64_t)j * KD + i]);
+  __shared__ double xs[64 * NR];
+  int l = blockIdx.x;
+  for (int i = threadIdx.x; i < KD * NR; i += blockDim.x) xs[i] = Ar<FMT>::to_d(xp[(int64_t)l * KD * NR + i]);
   __syncthreads();
-  const BT* Uj = UT + (int64_t)j * KD * KC;
+  const BT* Ul = UT + (int64_t)l * KD * KC;
   for (int b = threadIdx.x; b < KC; b += blockDim.x) {
-    double acc = 0.0;
-    for (int i = 0; i < KD; ++i) acc += (double)Uj[b + i * KC] * xs[i];
-    xc[(int64_t)j * KC + b] = Ar<FMT>::from_d(acc);
+    double acc[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[j] = 0.0;
+    for (int i = 0; i < KD; ++i) {
+      double u = (double)Ul[b + i * KC];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[j] += u * xs[i * NR + j];
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) xc[((int64_t)l * KC + b) * NR + j] = Ar<FMT>::from_d(acc[j]);
   }
 }
 
@@ -249,7 +282,7 @@ __global__ void k_up_leaf(const BT* __restrict__ UT, int KD, int KC,
 // blocks of k_bsgemv, and one warp streams one transfer with the same lane layout:
 // the upward pass uses the transposed product E'_c^T x_c (reduce-scatter over the
 // lanes that share a column), the downward pass the row product E'_c y_parent.
-template <int K, int FMT>
+template <int K, int FMT, int NR>
 __global__ void __launch_bounds__(256) k_up_blk(const void* __restrict__ Epool,
                                                 const typename Ar<FMT>::vec_t* __restrict__ xch,
                                                 typename Ar<FMT>::vec_t* __restrict__ xpar, int nch) {
@@ -261,18 +294,20 @@ __global__ void __launch_bounds__(256) k_up_blk(const void* __restrict__ Epool,
   constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
   constexpr int CH = T < LPC ? T : LPC;
   constexpr int V = A::V, P = 8 / V;
-  __shared__ acc_t v[8][K];
+  __shared__ acc_t v[8][K * NR];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * 8 + w;
   const int rb = 8 * (lane % LPC), cl = lane / LPC;
   if (c < nch) {
-    vec_t xt[8];
+    vec_t xt[8][NR];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) xt[r] = xch[(int64_t)c * K + rb + r];
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) xt[r][j] = xch[((int64_t)c * K + rb + r) * NR + j];
     const ld_t* B = (const ld_t*)((const char*)Epool + (int64_t)c * K * K * (FMT == FMT_F32 ? 4 : 8));
 #pragma unroll 1
     for (int ch = 0; ch < T / CH; ++ch) {
-      acc_t zc[CH];
+      acc_t zc[CH][NR];
 #pragma unroll
       for (int tt = 0; tt < CH; ++tt) {
         const int t = ch * CH + tt;
@@ -282,49 +317,55 @@ __global__ void __launch_bounds__(256) k_up_blk(const void* __restrict__ Epool,
           ld_t q = __ldg(B + (t * P + k) * 32 + lane);
           A::decode(q, m + k * V);
         }
-        acc_t zz = A::zero();
 #pragma unroll
-        for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r]);
-        zc[tt] = zz;
-      }
-      if (CH == LPC) {
+        for (int j = 0; j < NR; ++j) {
+          acc_t zz = A::zero();
 #pragma unroll
-        for (int h = CH / 2; h >= 1; h >>= 1) {
-          const bool up = (lane & h) != 0;
-#pragma unroll
-          for (int j = 0; j < h; ++j) {
-            acc_t send = up ? zc[j] : zc[j + h];
-            acc_t keep = up ? zc[j + h] : zc[j];
-            A::add(keep, A::shfl(send, h));
-            zc[j] = keep;
-          }
+          for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r][j]);
+          zc[tt][j] = zz;
         }
-        v[w][cl + CPP * (ch * CH + (lane & (CH - 1)))] = zc[0];
-      } else {
+      }
 #pragma unroll
-        for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0], A::shfl(zc[0], h));
-        if ((lane % LPC) == 0) v[w][cl + CPP * (ch * CH)] = zc[0];
+      for (int j = 0; j < NR; ++j) {
+        if (CH == LPC) {
+#pragma unroll
+          for (int h = CH / 2; h >= 1; h >>= 1) {
+            const bool up = (lane & h) != 0;
+#pragma unroll
+            for (int q = 0; q < h; ++q) {
+              acc_t send = up ? zc[q][j] : zc[q + h][j];
+              acc_t keep = up ? zc[q + h][j] : zc[q][j];
+              A::add(keep, A::shfl(send, h));
+              zc[q][j] = keep;
+            }
+          }
+          v[w][(cl + CPP * (ch * CH + (lane & (CH - 1)))) * NR + j] = zc[0][j];
+        } else {
+#pragma unroll
+          for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0][j], A::shfl(zc[0][j], h));
+          if ((lane % LPC) == 0) v[w][(cl + CPP * (ch * CH)) * NR + j] = zc[0][j];
+        }
       }
     }
   }
   __syncthreads();
   if (c < nch && (w & 1) == 0) {
     const int p = c >> 1;
-    for (int j = lane; j < K; j += 32) {
-      acc_t s = v[w][j];
-      A::add(s, v[w + 1][j]);
-      xpar[(int64_t)p * K + j] = A::out(s);
+    for (int i = lane; i < K * NR; i += 32) {
+      acc_t s = v[w][i];
+      A::add(s, v[w + 1][i]);
+      xpar[(int64_t)p * K * NR + i] = A::out(s);
     }
   }
 }
 
-template <int K, int FMT>
+template <int K, int FMT, int NR>
 __global__ void __launch_bounds__(256) k_down_blk(int slot_base, int ncl,
                                                   const typename Ar<FMT>::yo_t* __restrict__ yrow,
                                                   const void* __restrict__ Epool,
                                                   const typename Ar<FMT>::vec_t* __restrict__ ypar,
                                                   typename Ar<FMT>::vec_t* __restrict__ yc,
-                                                  double* __restrict__ yout) {
+                                                  double* __restrict__ yout, int64_t ldo) {
   using A = Ar<FMT>;
   using vec_t = typename A::vec_t;
   using mel_t = typename A::mel_t;
@@ -332,18 +373,20 @@ __global__ void __launch_bounds__(256) k_down_blk(int slot_base, int ncl,
   using ld_t = typename A::ld_t;
   constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
   constexpr int V = A::V, P = 8 / V;
-  __shared__ acc_t s[8][K];
+  __shared__ acc_t s[8][K * NR];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * 8 + w;
   if (c >= ncl) return;
   const int sl = slot_base + c;
   if (Epool) {
     const int rb = 8 * (lane % LPC), cl = lane / LPC;
-    acc_t ya[8];
+    acc_t ya[8][NR];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) ya[r] = A::zero();
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) ya[r][j] = A::zero();
     const ld_t* B = (const ld_t*)((const char*)Epool + (int64_t)c * K * K * (FMT == FMT_F32 ? 4 : 8));
-    const vec_t* yp = ypar + (int64_t)(c >> 1) * K;
+    const vec_t* yp = ypar + (int64_t)(c >> 1) * K * NR;
 #pragma unroll 4
     for (int t = 0; t < T; ++t) {
       mel_t m[8];
@@ -352,27 +395,36 @@ __global__ void __launch_bounds__(256) k_down_blk(int slot_base, int ncl,
         ld_t q = __ldg(B + (t * P + k) * 32 + lane);
         A::decode(q, m + k * V);
       }
-      const vec_t xv = yp[cl + CPP * t];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) A::fma(ya[r], m[r], xv);
+      for (int j = 0; j < NR; ++j) {
+        const vec_t xv = yp[(cl + CPP * t) * NR + j];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) A::fma(ya[r][j], m[r], xv);
+      }
     }
 #pragma unroll
     for (int h = LPC; h < 32; h <<= 1)
 #pragma unroll
-      for (int r = 0; r < 8; ++r) A::add(ya[r], A::shfl(ya[r], h));
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) A::add(ya[r][j], A::shfl(ya[r][j], h));
     if (lane < LPC)
 #pragma unroll
-      for (int r = 0; r < 8; ++r) s[w][rb + r] = ya[r];
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) s[w][(rb + r) * NR + j] = ya[r][j];
     __syncwarp();
   }
-  for (int a = lane; a < K; a += 32) {
-    acc_t acc = A::from_d((double)yrow[(int64_t)sl * K + a]);
-    if (Epool) A::add(acc, s[w][a]);
+  for (int i = lane; i < K * NR; i += 32) {
+    acc_t acc = A::from_d((double)yrow[(int64_t)sl * K * NR + i]);
+    if (Epool) A::add(acc, s[w][i]);
     vec_t o = A::out(acc);
-    if (yout)
-      yout[(int64_t)c * K + a] = A::to_d(o);
-    else
-      yc[(int64_t)sl * K + a] = o;
+    if (yout) {
+      const int a = i / NR, j = i % NR;
+      yout[(int64_t)c * K + a + j * ldo] = A::to_d(o);
+    } else {
+      yc[(int64_t)sl * K * NR + i] = o;
+    }
   }
 }
 
@@ -397,28 +449,34 @@ __global__ void k_swizzle_blocks(const double* __restrict__ in, int K, void* __r
   }
 }
 
-// y(point) = yrowD + U y_hat(leaf), scattered to user order.
-template <int FMT, class BT>
+// y(point) = yrowD + U y_hat(leaf), scattered to user order (column j at y + j*ldy).
+template <int FMT, class BT, int NR>
 __global__ void k_leaf_final(int KD, int KC, const typename Ar<FMT>::yo_t* __restrict__ yrow,
                              const BT* __restrict__ U, const typename Ar<FMT>::vec_t* __restrict__ yleaf,
                              const int* __restrict__ leafoff, const int* __restrict__ perm,
-                             double* __restrict__ y) {
+                             double* __restrict__ y, int64_t ldy) {
   using A = Ar<FMT>;
-  __shared__ double ps[64];
-  int j = blockIdx.x;
+  __shared__ double ps[64 * NR];
+  int l = blockIdx.x;
   if (U)
-    for (int i = threadIdx.x; i < KC; i += blockDim.x) ps[i] = A::to_d(yleaf[(int64_t)j * KC + i]);
+    for (int i = threadIdx.x; i < KC * NR; i += blockDim.x) ps[i] = A::to_d(yleaf[(int64_t)l * KC * NR + i]);
   __syncthreads();
-  int p0 = leafoff[j], nj = leafoff[j + 1] - p0;
-  for (int i = threadIdx.x; i < nj; i += blockDim.x) {
-    double v = (double)yrow[(int64_t)j * KD + i];
+  int p0 = leafoff[l], nl = leafoff[l + 1] - p0;
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    double v[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) v[j] = (double)yrow[((int64_t)l * KD + i) * NR + j];
     if (U) {
-      const BT* Uj = U + (int64_t)j * KD * KC;
-      double t = 0.0;
-      for (int b = 0; b < KC; ++b) t += (double)Uj[i + b * KD] * ps[b];
-      v += t;
+      const BT* Ul = U + (int64_t)l * KD * KC;
+      for (int b = 0; b < KC; ++b) {
+        double u = (double)Ul[i + b * KD];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) v[j] += u * ps[b * NR + j];
+      }
     }
-    y[perm[p0 + i]] = v;
+    const int64_t o = perm[p0 + i];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) y[o + j * ldy] = v[j];
   }
 }
 
@@ -587,8 +645,9 @@ void setup_operators(Matrix& M) {
       M.d_ET32 = ET32;
     }
   }
-  size_t ncoef = (size_t)std::max(M.nslots(), 1) * M.KC;
-  size_t npts = (size_t)(1 << L) * M.KD;
+  // product workspaces hold up to NRMAX interleaved columns
+  size_t ncoef = (size_t)std::max(M.nslots(), 1) * M.KC * NRMAX;
+  size_t npts = (size_t)(1 << L) * M.KD * NRMAX;
   M.wx.p = M.alloc(8 * ncoef);
   M.wyrow.p = M.alloc(8 * ncoef);
   M.wyc.p = M.alloc(8 * ncoef);
@@ -597,12 +656,12 @@ void setup_operators(Matrix& M) {
   H2_CUDA(cudaStreamSynchronize(s));
 }
 
-template <int FMT>
+template <int FMT, int NR>
 static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, void* yrow, cudaStream_t s) {
   using vt = typename Ar<FMT>::vec_t;
   using yt = typename Ar<FMT>::yo_t;
   if (op.nrows == 0) return;
-  H2_CUDA(cudaMemsetAsync(yrow, 0, sizeof(yt) * (size_t)op.nrows * op.K, s));
+  H2_CUDA(cudaMemsetAsync(yrow, 0, sizeof(yt) * (size_t)op.nrows * op.K * NR, s));
   // enough CTAs to fill the GPU when the operator has few block rows
   const int split = std::max(1, std::min(16, ceil_div(2048, op.nrows)));
   const int grid = op.nrows * split;
@@ -620,13 +679,13 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
   }
   switch (op.K) {
     case 16:
-      { k_bsgemv<16, FMT><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
+      { k_bsgemv<16, FMT, NR><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
       break;
     case 32:
-      { k_bsgemv<32, FMT><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
+      { k_bsgemv<32, FMT, NR><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
       break;
     case 64:
-      { k_bsgemv<64, FMT><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
+      { k_bsgemv<64, FMT, NR><<<grid, 256, 0, s>>>(op.rowptr, op.col, blk, (const vt*)x, (yt*)yrow, split); ::h2mg::count_launch(); }
       break;
     default:
       throw Error{H2MG_ERR_UNSUPPORTED, "block size not supported"};
@@ -635,105 +694,139 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
   if (P.on) {
     H2_CUDA(cudaEventRecord(P.ev[2 * P.used + 1], s));
     P.used++;
-    P.bytes.push_back((double)op.bytes(FMT == FMT_F32 ? 4 : 8, sizeof(vt)));
+    P.bytes.push_back((double)op.bytes(FMT == FMT_F32 ? 4 : 8, sizeof(vt) * NR));
   }
 }
 
-template <int FMT>
+template <int FMT, int NR>
 static void launch_up(const void* Epool, int KC, const void* xch, void* xpar, int nch, cudaStream_t s) {
   using vt = typename Ar<FMT>::vec_t;
   int grid = ceil_div(nch, 8);
   switch (KC) {
-    case 16: { k_up_blk<16, FMT><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
-    case 32: { k_up_blk<32, FMT><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
-    default: { k_up_blk<64, FMT><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
+    case 16: { k_up_blk<16, FMT, NR><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
+    case 32: { k_up_blk<32, FMT, NR><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
+    default: { k_up_blk<64, FMT, NR><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
   }
   H2_LAUNCH_CHECK();
 }
 
-template <int FMT>
+template <int FMT, int NR>
 static void launch_down(int slot_base, int KC, int ncl, const void* yrow, const void* Epool, const void* ypar,
-                        void* yc, double* yout, cudaStream_t s) {
+                        void* yc, double* yout, int64_t ldo, cudaStream_t s) {
   using vt = typename Ar<FMT>::vec_t;
   using yt = typename Ar<FMT>::yo_t;
   int grid = ceil_div(ncl, 8);
   switch (KC) {
-    case 16: { k_down_blk<16, FMT><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout); ::h2mg::count_launch(); } break;
-    case 32: { k_down_blk<32, FMT><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout); ::h2mg::count_launch(); } break;
-    default: { k_down_blk<64, FMT><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout); ::h2mg::count_launch(); } break;
+    case 16: { k_down_blk<16, FMT, NR><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout, ldo); ::h2mg::count_launch(); } break;
+    case 32: { k_down_blk<32, FMT, NR><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout, ldo); ::h2mg::count_launch(); } break;
+    default: { k_down_blk<64, FMT, NR><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout, ldo); ::h2mg::count_launch(); } break;
   }
   H2_LAUNCH_CHECK();
 }
 
-template <int FMT, class BT>
-static void apply_impl(Matrix& M, int i, const double* x, double* y, cudaStream_t s, const BT* U,
-                       const BT* UT, const BT* E, const BT* ET, const ApplyWork* ws = nullptr) {
+// y = A_i x for NR columns (x, y column-major with leading dimensions ldx, ldy).
+template <int FMT, class BT, int NR>
+static void apply_impl(Matrix& M, int i, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t s,
+                       const BT* U, const BT* UT, const ApplyWork* ws = nullptr) {
   using vt = typename Ar<FMT>::vec_t;
+  using yt = typename Ar<FMT>::yo_t;
   const int L = M.L, KC = M.KC, KD = M.KD, ts = M.tstar;
   const bool f32 = (FMT == FMT_F32);
-  using yt = typename Ar<FMT>::yo_t;
   vt* xc = (vt*)(ws ? ws->xc : M.wx.p);
   yt* yr = (yt*)(ws ? ws->yr : M.wyrow.p);
   vt* yc = (vt*)(ws ? ws->yc : M.wyc.p);
   const char* epool = (const char*)(FMT == FMT_F32 ? M.poolE32.p : M.poolE.p);
   const size_t eb = FMT == FMT_F32 ? 4 : 8;
+  auto cslot = [&](int ell) { return (size_t)M.slot0(ell) * KC * NR; };   // first element of a level
   if (i == 1) {
     vt* xp = (vt*)(ws ? ws->xp : M.wxp.p);
     yt* yp = (yt*)(ws ? ws->yp : M.wyp.p);
-    { k_pts_in<FMT><<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, xp); ::h2mg::count_launch(); }
+    { k_pts_in<FMT, NR><<<ceil_div(M.n, 256), 256, 0, s>>>(x, ldx, M.d_slot_of, M.n, xp); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     if (ts >= 0) {
-      { k_up_leaf<FMT, BT><<<1 << L, std::max(KC, 32), 0, s>>>(UT, KD, KC, xp, xc + (size_t)M.slot0(L) * KC); ::h2mg::count_launch(); }
+      { k_up_leaf<FMT, BT, NR><<<1 << L, std::max(KC, 32), 0, s>>>(UT, KD, KC, xp, xc + cslot(L)); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
       for (int ell = L - 1; ell >= ts; --ell)
-        launch_up<FMT>(epool + (size_t)M.slot0(ell + 1) * KC * KC * eb, KC, xc + (size_t)M.slot0(ell + 1) * KC,
-                       xc + (size_t)M.slot0(ell) * KC, 1 << (ell + 1), s);
+        launch_up<FMT, NR>(epool + (size_t)M.slot0(ell + 1) * KC * KC * eb, KC, xc + cslot(ell + 1), xc + cslot(ell),
+                           1 << (ell + 1), s);
     }
-    launch_bsgemv<FMT>(M, M.opD, f32, xp, yp, s);
+    launch_bsgemv<FMT, NR>(M, M.opD, f32, xp, yp, s);
     if (ts >= 0) {
-      launch_bsgemv<FMT>(M, M.opC[1], f32, xc, yr, s);
+      launch_bsgemv<FMT, NR>(M, M.opC[1], f32, xc, yr, s);
       for (int ell = ts; ell <= L; ++ell)
-        launch_down<FMT>(M.slot0(ell), KC, 1 << ell, yr,
-                         ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr,
-                         ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, nullptr, s);
+        launch_down<FMT, NR>(M.slot0(ell), KC, 1 << ell, yr,
+                             ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr,
+                             ell > ts ? yc + cslot(ell - 1) : nullptr, yc, nullptr, 0, s);
     }
-    { k_leaf_final<FMT, BT><<<1 << L, std::max(KD, 32), 0, s>>>(
-        KD, KC, yp, ts >= 0 ? U : nullptr,
-        ts >= 0 ? yc + (size_t)M.slot0(L) * KC : nullptr, M.d_leafoff, M.d_perm, y); ::h2mg::count_launch(); }
+    { k_leaf_final<FMT, BT, NR><<<1 << L, std::max(KD, 32), 0, s>>>(
+        KD, KC, yp, ts >= 0 ? U : nullptr, ts >= 0 ? yc + cslot(L) : nullptr, M.d_leafoff, M.d_perm, y, ldy);
+      ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     return;
   }
   const int m = L - i + 2;
   const int64_t nm = (int64_t)(1 << m) * KC;
-  { k_coef_in<FMT><<<ceil_div(nm, 256), 256, 0, s>>>(x, nm, xc + (size_t)M.slot0(m) * KC); ::h2mg::count_launch(); }
+  { k_coef_in<FMT, NR><<<ceil_div(nm, 256), 256, 0, s>>>(x, ldx, nm, xc + cslot(m)); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   for (int ell = m - 1; ell >= ts; --ell)
-    launch_up<FMT>(epool + (size_t)M.slot0(ell + 1) * KC * KC * eb, KC, xc + (size_t)M.slot0(ell + 1) * KC,
-                   xc + (size_t)M.slot0(ell) * KC, 1 << (ell + 1), s);
-  launch_bsgemv<FMT>(M, M.opC[i], f32, xc, yr, s);
+    launch_up<FMT, NR>(epool + (size_t)M.slot0(ell + 1) * KC * KC * eb, KC, xc + cslot(ell + 1), xc + cslot(ell),
+                       1 << (ell + 1), s);
+  launch_bsgemv<FMT, NR>(M, M.opC[i], f32, xc, yr, s);
   for (int ell = ts; ell <= m; ++ell)
-    launch_down<FMT>(M.slot0(ell), KC, 1 << ell, yr,
-                     ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr,
-                     ell > ts ? yc + (size_t)M.slot0(ell - 1) * KC : nullptr, yc, ell == m ? y : nullptr, s);
+    launch_down<FMT, NR>(M.slot0(ell), KC, 1 << ell, yr,
+                         ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr,
+                         ell > ts ? yc + cslot(ell - 1) : nullptr, yc, ell == m ? y : nullptr, ldy, s);
+}
+
+template <int FMT, class BT>
+static void apply_cols(Matrix& M, int i, const double* x, int64_t ldx, double* y, int64_t ldy, int nr,
+                       cudaStream_t s, const BT* U, const BT* UT) {
+  int c = 0;
+  while (c < nr) {
+    int left = nr - c;
+    if constexpr (FMT == FMT_F32) {
+      if (left >= 4) {
+        apply_impl<FMT, BT, 4>(M, i, x + c * ldx, ldx, y + c * ldy, ldy, s, U, UT);
+        c += 4;
+        continue;
+      }
+    }
+    if (left >= 2) {
+      apply_impl<FMT, BT, 2>(M, i, x + c * ldx, ldx, y + c * ldy, ldy, s, U, UT);
+      c += 2;
+    } else {
+      apply_impl<FMT, BT, 1>(M, i, x + c * ldx, ldx, y + c * ldy, ldy, s, U, UT);
+      c += 1;
+    }
+  }
+}
+
+// Y = A_i X for nr columns; columns go through the block products NR at a time
+// (4 for the FP32 copy, 2 for float64 / double-float), each block read once per group.
+void apply_level_multi(Matrix& M, int i, bool f32, const double* x, int64_t ldx, double* y, int64_t ldy, int nr,
+                       cudaStream_t s) {
+  if (f32) {
+    H2_REQUIRE(M.with_f32, H2MG_ERR_INVALID_ARG, "matrix was built without an FP32 copy");
+    apply_cols<FMT_F32, float>(M, i, x, ldx, y, ldy, nr, s, M.d_U32, M.d_UT32);
+  } else if (M.fmt == FMT_DF) {
+    apply_cols<FMT_DF, double>(M, i, x, ldx, y, ldy, nr, s, M.d_U, M.d_UT);
+  } else {
+    apply_cols<FMT_F64, double>(M, i, x, ldx, y, ldy, nr, s, M.d_U, M.d_UT);
+  }
 }
 
 void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s) {
-  if (f32) {
-    H2_REQUIRE(M.with_f32, H2MG_ERR_INVALID_ARG, "matrix was built without an FP32 copy");
-    apply_impl<FMT_F32, float>(M, i, x, y, s, M.d_U32, M.d_UT32, M.d_E32, M.d_ET32);
-  } else if (M.fmt == FMT_DF) {
-    apply_impl<FMT_DF, double>(M, i, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET);
-  } else {
-    apply_impl<FMT_F64, double>(M, i, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET);
-  }
+  int64_t n = level_size(M, i);
+  apply_level_multi(M, i, f32, x, n, y, n, 1, s);
 }
 
 // Level-1 product in the primary format with caller-supplied workspace (the
 // handle's own buffers are not touched).
 void apply_level1_ws(Matrix& M, const double* x, double* y, cudaStream_t s, const ApplyWork& ws) {
   if (M.fmt == FMT_DF)
-    apply_impl<FMT_DF, double>(M, 1, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET, &ws);
+    apply_impl<FMT_DF, double, 1>(M, 1, x, M.n, y, M.n, s, M.d_U, M.d_UT, &ws);
   else
-    apply_impl<FMT_F64, double>(M, 1, x, y, s, M.d_U, M.d_UT, M.d_E, M.d_ET, &ws);
+    apply_impl<FMT_F64, double, 1>(M, 1, x, M.n, y, M.n, s, M.d_U, M.d_UT, &ws);
 }
 
 // Bytes of each workspace region of the level-1 product.

@@ -1,6 +1,8 @@
 // capi.cu -- the extern "C" entry points declared in include/h2mg.h.
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -13,6 +15,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void* Matrix::alloc(size_t bytes) {
   void* p = nullptr;
@@ -29,11 +32,18 @@ void* Matrix::alloc(size_t bytes) {
   return p;
 }
 
+void best_effort(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  if (std::getenv("H2MG_DEBUG")) std::fprintf(stderr, "[h2mg] %s failed: %s\n", what, cudaGetErrorString(e));
+  cudaGetLastError();
+}
+
 Matrix::~Matrix() {
-  if (stream) cudaStreamSynchronize(stream);
-  for (auto e : prof.ev) cudaEventDestroy(e);
+  if (stream) best_effort(cudaStreamSynchronize(stream), "cudaStreamSynchronize (release)");
+  destroy_graphs(*this);
+  for (auto e : prof.ev) best_effort(cudaEventDestroy(e), "cudaEventDestroy (profile)");
   for (auto& d : owned)
-    if (d.p) cudaFree(d.p);
+    if (d.p) best_effort(cudaFree(d.p), "cudaFree (release)");
 }
 
 bool is_device_pointer(const void* p);
@@ -69,7 +79,42 @@ struct DevView {
     }
   }
   ~DevView() {
-    if (staged && d) cudaFree(d);
+    if (staged && d) best_effort(cudaFree(d), "cudaFree (staging)");
+  }
+};
+
+// A group of g columns of length n at stride ld, seen from the device. Device
+// columns are used in place unless a packed layout (leading dimension n) is needed
+// and ld != n; host columns (and those) are staged through a packed device copy.
+struct ColsView {
+  double* d = nullptr;
+  int64_t ldd = 0;
+  bool staged = false;
+  const double* src;
+  int64_t n, ld;
+  int g;
+  ColsView(const double* p, int64_t n_, int64_t ld_, int g_, bool copy_in, bool packed, cudaStream_t s)
+      : src(p), n(n_), ld(ld_), g(g_) {
+    if (is_device_ptr(p) && (!packed || ld == n || g == 1)) {
+      d = const_cast<double*>(p);
+      ldd = ld;
+      return;
+    }
+    staged = true;
+    ldd = n;
+    H2_CUDA(cudaMalloc(&d, sizeof(double) * std::max<int64_t>(n * g, 1)));
+    if (copy_in)
+      H2_CUDA(cudaMemcpy2DAsync(d, sizeof(double) * n, p, sizeof(double) * ld, sizeof(double) * n, g,
+                                cudaMemcpyDefault, s));
+  }
+  void copy_out(double* dst, cudaStream_t s) {
+    if (!staged) return;
+    H2_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * ld, d, sizeof(double) * n, sizeof(double) * n, g,
+                              cudaMemcpyDefault, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+  }
+  ~ColsView() {
+    if (staged && d) best_effort(cudaFree(d), "cudaFree (staging)");
   }
 };
 
@@ -127,7 +172,10 @@ static void build_all(Matrix& M, const double* points, const h2mg_kernel* k, con
   if (!M.apply_only) build_coarse_near(M);
   build_f32_copies(M);
   setup_operators(M);
-  if (!M.apply_only) build_dense_coarse(M);
+  if (!M.apply_only) {
+    build_dense_coarse(M);
+    alloc_solve_workspace(M);
+  }
   H2_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -162,6 +210,10 @@ template <class F>
 static h2mg_status guard(F f) {
   try {
     g_last_error.clear();
+    // an error left by an unchecked release (destructors) is not this call's
+    const cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess && std::getenv("H2MG_DEBUG"))
+      std::fprintf(stderr, "[h2mg] CUDA error pending at entry: %s\n", cudaGetErrorString(stale));
     return f();
   } catch (const Error& e) {
     set_error(e.msg);
@@ -255,10 +307,11 @@ h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int6
     Matrix& M = A->M;
     H2_REQUIRE(nrhs >= 1 && ld >= M.n, H2MG_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= n");
     cudaStream_t s = (cudaStream_t)stream;
-    for (int c = 0; c < nrhs; ++c) {
-      DevView X(x + (int64_t)c * ld, M.n, true, s), Y(y + (int64_t)c * ld, M.n, false, s);
-      apply_level(M, 1, false, X.d, Y.d, s);
-      Y.copy_out(y + (int64_t)c * ld, M.n, s);
+    for (int c = 0; c < nrhs; c += NRMAX) {
+      const int g = std::min(NRMAX, nrhs - c);
+      ColsView X(x + (int64_t)c * ld, M.n, ld, g, true, false, s), Y(y + (int64_t)c * ld, M.n, ld, g, false, false, s);
+      apply_level_multi(M, 1, false, X.d, X.ldd, Y.d, Y.ldd, g, s);
+      Y.copy_out(y + (int64_t)c * ld, s);
     }
     return H2MG_OK;
   });
@@ -278,10 +331,14 @@ h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int6
     if (!M.coarse_ok) throw Error{H2MG_ERR_NOT_SPD, "the coarsest operator is not positive definite"};
     cudaStream_t s = (cudaStream_t)stream;
     h2mg_status worst = H2MG_OK;
-    for (int c = 0; c < nrhs; ++c) {
-      DevView B(b + (int64_t)c * ld, M.n, true, s), X(x + (int64_t)c * ld, M.n, true, s);
-      h2mg_status st = solve(M, B.d, X.d, *o, info, s);
-      X.copy_out(x + (int64_t)c * ld, M.n, s);
+    h2mg_solve_info inf[NRMAX];
+    for (int c = 0; c < nrhs; c += NRMAX) {
+      const int g = std::min(NRMAX, nrhs - c);
+      ColsView B(b + (int64_t)c * ld, M.n, ld, g, true, true, s), X(x + (int64_t)c * ld, M.n, ld, g, true, true, s);
+      h2mg_status st = solve_multi(M, B.d, X.d, g, *o, inf, s);
+      X.copy_out(x + (int64_t)c * ld, s);
+      if (info)
+        for (int j = 0; j < g; ++j) info[c + j] = inf[j];
       if (st != H2MG_OK && worst == H2MG_OK) worst = st;
     }
     if (worst != H2MG_OK) set_error(h2mg_error_string(worst));

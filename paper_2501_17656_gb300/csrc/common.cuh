@@ -17,6 +17,8 @@ struct Error {
 
 void set_error(const std::string& msg);
 void count_launch();   // every kernel launch of the library is counted (h2mg_launch_count)
+void add_launches(int64_t k);
+void best_effort(cudaError_t e, const char* what);   // unchecked release: report under H2MG_DEBUG, clear   // kernels run by a graph replay (negative: undo capture-time counts)
 
 #define H2_CUDA(call)                                                                   \
   do {                                                                                  \

@@ -240,6 +240,30 @@ __global__ void k_symv_cols(const double* __restrict__ Ainv, int64_t n, const do
   if (lane == 0) e[i] = s;
 }
 
+// E[:, c] = A^{-1} R[:, c] for NR columns (leading dimension n): one warp per output
+// row reads that column of the symmetric inverse once for all NR right-hand sides.
+template <int NR>
+__global__ void k_symv_multi(const double* __restrict__ Ainv, int64_t n, const double* __restrict__ r,
+                             double* __restrict__ e) {
+  int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const double* col = Ainv + i * n;
+  double s[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) s[c] = 0.0;
+  for (int64_t j = lane; j < n; j += 32) {
+    const double a = col[j];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) s[c] = fma(a, r[c * n + j], s[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c) {
+    for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+    if (lane == 0) e[c * n + i] = s[c];
+  }
+}
+
 static void build_inverse(Matrix& M) {
   cudaStream_t s = M.stream;
   int64_t n = M.nl;
@@ -421,6 +445,25 @@ void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s) {
     { k_from_slots<<<ceil_div(M.n, 256), 256, 0, s>>>(x, M.d_slot_of, M.n, e); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
+}
+
+// The coarse solve for nr columns of the coarsest level (leading dimension nl); r and
+// e must not overlap. Level l = 1 (the whole matrix is dense) goes column by column.
+void coarse_solve_multi(Matrix& M, const double* r, double* e, int nr, cudaStream_t s) {
+  const int64_t n = M.nl;
+  if (M.lev == 1) {
+    for (int c = 0; c < nr; ++c) coarse_solve(M, r + c * M.n, e + c * M.n, s);
+    return;
+  }
+  const int g = ceil_div(n, 8);
+  switch (nr) {
+    case 1: { k_symv_multi<1><<<g, 256, 0, s>>>(M.d_Ainv, n, r, e); ::h2mg::count_launch(); } break;
+    case 2: { k_symv_multi<2><<<g, 256, 0, s>>>(M.d_Ainv, n, r, e); ::h2mg::count_launch(); } break;
+    case 3: { k_symv_multi<3><<<g, 256, 0, s>>>(M.d_Ainv, n, r, e); ::h2mg::count_launch(); } break;
+    case 4: { k_symv_multi<4><<<g, 256, 0, s>>>(M.d_Ainv, n, r, e); ::h2mg::count_launch(); } break;
+    default: throw Error{H2MG_ERR_INVALID_ARG, "too many columns for one coarse solve"};
+  }
+  H2_LAUNCH_CHECK();
 }
 
 }  // namespace h2mg

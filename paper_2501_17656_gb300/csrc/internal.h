@@ -42,6 +42,8 @@ struct Profile {
   std::vector<double> bytes;
 };
 
+struct GraphSet;   // captured V-cycles of a matrix (solve.cu)
+
 // Host-side copy of a full (both triangles) CSR list of cluster pairs.
 struct HostCSR {
   std::vector<int> rowptr, col;
@@ -124,6 +126,8 @@ struct Matrix {
   int* d_flag = nullptr;        // device error flags
 
   Profile prof;
+  GraphSet* graphs = nullptr;   // captured V-cycle graphs, by solve settings
+  cudaStream_t cap_stream = nullptr;
   std::vector<DevBuf> owned;    // everything else
   ~Matrix();
   void* alloc(size_t bytes);    // owned allocation, zero-initialised
@@ -140,6 +144,7 @@ void build_f32_copies(Matrix& M);
 // ---- dense.cu
 void build_dense_coarse(Matrix& M);
 void coarse_solve(Matrix& M, const double* r, double* e, cudaStream_t s);
+void coarse_solve_multi(Matrix& M, const double* r, double* e, int nr, cudaStream_t s);
 // ---- apply.cu
 struct ApplyWork {                // workspace of one product (see apply_impl)
   void *xc, *yr, *yc, *xp, *yp;
@@ -148,6 +153,10 @@ void setup_operators(Matrix& M);
 void apply_level1_ws(Matrix& M, const double* x, double* y, cudaStream_t s, const ApplyWork& ws);
 void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts);
 void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s);
+// Right-hand sides that one product, smoother, V-cycle or solve handles together.
+constexpr int NRMAX = 4;
+void apply_level_multi(Matrix& M, int i, bool f32, const double* x, int64_t ldx, double* y, int64_t ldy, int nr,
+                       cudaStream_t s);
 int64_t apply_bytes(const Matrix& M, int i);
 // ---- solve.cu
 void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n, double* x,
@@ -158,6 +167,15 @@ void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double*
             cudaStream_t s);
 h2mg_status solve(Matrix& M, const double* b, double* x, const h2mg_solve_opts& o,
                   h2mg_solve_info* info, cudaStream_t s);
+void alloc_solve_workspace(Matrix& M);
+void destroy_graphs(Matrix& M);
+// nr <= NRMAX columns, column-major with leading dimension N_i (n for the solve)
+void smooth_multi(Matrix& M, int i, bool f32, const double* f, const double* x0, int n, double* x, double* r,
+                  int nr, cudaStream_t s);
+void vcycle_multi(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double* r1, double* xout, int nr,
+                  cudaStream_t s);
+h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2mg_solve_opts& o,
+                        h2mg_solve_info* info, cudaStream_t s);
 int64_t level_size(const Matrix& M, int i);
 double device_dot(const double* a, const double* b, int64_t n, cudaStream_t s);
 

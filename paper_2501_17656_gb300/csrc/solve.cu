@@ -1,7 +1,9 @@
 // solve.cu -- the smoother Iter(A_i, f, x0) (textbook CG), restriction U_i^T and
 // prolongation V_i^T = U_i, one V-cycle of Algorithm 1 and the outer iteration
-// (Sec. 3.3). All multigrid vectors are float64 on the device; the scalars of CG
-// live in device memory so that a V-cycle never waits for the host.
+// (Sec. 3.3). All multigrid vectors are float64 on the device, column-major with
+// leading dimension N_i; up to NRMAX right-hand sides go through every step together
+// (one product launch per step reads each stored block once for all of them), each
+// with its own CG scalars kept in device memory, so a V-cycle never waits for the host.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -31,13 +33,16 @@ __device__ double block_reduce_sum(double v) {
   return s;   // valid in thread 0
 }
 
-__global__ void k_dot_part(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+// part[col * NPART + block] = partial of a_col^T b_col (column = blockIdx.y)
+__global__ void k_dot_part(const double* __restrict__ a, const double* __restrict__ b, int64_t n, int64_t ld,
                            double* __restrict__ part) {
+  const double* ac = a + blockIdx.y * ld;
+  const double* bc = b + blockIdx.y * ld;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s = fma(a[i], b[i], s);
+    s = fma(ac[i], bc[i], s);
   s = block_reduce_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (threadIdx.x == 0) part[blockIdx.y * NPART + blockIdx.x] = s;
 }
 
 __device__ double sum_parts(const double* part, int np) {
@@ -48,16 +53,16 @@ __device__ double sum_parts(const double* part, int np) {
 
 static int part_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(NPART, (n + 1023) / 1024)); }
 
-// init: rho = r.r, thresh = (1e-30 |f|)^2
-__global__ void k_cg_init(const double* __restrict__ prr, int nrr, const double* __restrict__ pff, int nff,
+// per column (thread c): rho = r.r, thresh = (1e-30 |f|)^2
+__global__ void k_cg_init(const double* __restrict__ prr, const double* __restrict__ pff, int np, int nr,
                           CGState* st) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double rr = sum_parts(prr, nrr), ff = sum_parts(pff, nff);
-    double t = 1e-30 * sqrt(ff);
-    st->rho[0] = rr;
-    st->thresh = t * t;
-    st->stopped = 0;
-  }
+  const int c = threadIdx.x;
+  if (c >= nr) return;
+  double rr = sum_parts(prr + c * NPART, np), ff = sum_parts(pff + c * NPART, np);
+  double t = 1e-30 * sqrt(ff);
+  st[c].rho[0] = rr;
+  st[c].thresh = t * t;
+  st[c].stopped = 0;
 }
 
 // Sum of np (<= 256) partials, by every CTA (blockDim 256).
@@ -74,18 +79,25 @@ __device__ double cta_sum_parts(const double* __restrict__ part, int np) {
 }
 
 // alpha = rho / p^T q (stop before the update if p^T q <= 0); x += alpha p;
-// r -= alpha q; partials of r^T r. Every CTA takes the same decision.
+// r -= alpha q; partials of r^T r. Every CTA of a column (blockIdx.y) takes the same
+// decision from the same partials.
 __global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ x, double* __restrict__ r,
                                                    const double* __restrict__ p, const double* __restrict__ q,
-                                                   int64_t n, CGState* st, const double* __restrict__ ppq, int np,
-                                                   int par, double* __restrict__ part) {
-  const double pq = cta_sum_parts(ppq, np);
-  bool go = !st->stopped;
+                                                   int64_t n, int64_t ld, CGState* st,
+                                                   const double* __restrict__ ppq, int np, int par,
+                                                   double* __restrict__ part) {
+  const int c = blockIdx.y;
+  x += c * ld;
+  r += c * ld;
+  p += c * ld;
+  q += c * ld;
+  const double pq = cta_sum_parts(ppq + c * NPART, np);
+  bool go = !st[c].stopped;
   if (go && !(pq > 0.0)) {
     go = false;
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->stopped = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st[c].stopped = 1;
   }
-  const double al = go ? st->rho[par] / pq : 0.0;
+  const double al = go ? st[c].rho[par] / pq : 0.0;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double ri = r[i];
@@ -97,28 +109,37 @@ __global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ x, doubl
     s = fma(ri, ri, s);
   }
   s = block_reduce_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (threadIdx.x == 0) part[c * NPART + blockIdx.x] = s;
 }
 
 // rho' = r^T r; stop (after the update) if rho' <= thresh; else p = r + (rho'/rho) p.
 __global__ void __launch_bounds__(256) k_cg_p(double* __restrict__ p, const double* __restrict__ r, int64_t n,
-                                              CGState* st, const double* __restrict__ prr, int np, int par) {
-  const double rn = cta_sum_parts(prr, np);
-  if (st->stopped) return;
-  if (rn <= st->thresh) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->stopped = 1;
+                                              int64_t ld, CGState* st, const double* __restrict__ prr, int np,
+                                              int par) {
+  const int c = blockIdx.y;
+  p += c * ld;
+  r += c * ld;
+  const double rn = cta_sum_parts(prr + c * NPART, np);
+  if (st[c].stopped) return;
+  if (rn <= st[c].thresh) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st[c].stopped = 1;
     return;
   }
-  const double be = rn / st->rho[par];
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->rho[par ^ 1] = rn;
+  const double be = rn / st[c].rho[par];
+  if (blockIdx.x == 0 && threadIdx.x == 0) st[c].rho[par ^ 1] = rn;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = fma(be, p[i], r[i]);
 }
 
-// y = a*x + b*y  (elementwise)
-__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
+// y_c += a[c] x_c for every column c = blockIdx.y (a in device memory)
+__global__ void k_axpy_cols(const double* __restrict__ a, const double* __restrict__ x, double* __restrict__ y,
+                            int64_t n, int64_t ld) {
+  const int c = blockIdx.y;
+  const double al = a[c];
+  x += c * ld;
+  y += c * ld;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + b * y[i];
+    y[i] = fma(al, x[i], y[i]);
 }
 // z = x - y
 __global__ void k_sub(const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ z, int64_t n) {
@@ -134,11 +155,14 @@ __global__ void k_add(const double* __restrict__ x, const double* __restrict__ y
 static int vec_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(2048, (n + 255) / 256)); }
 
 // ----------------------------------------------------------------------------- transfers
-// r2[j*KC + b] = sum_i U_j[i, b] v[perm[leafoff[j] + i]]
+// Column blockIdx.y of each: input leading dimension ldv / lde, output ldo / ldv.
+// out[j*KC + b] = sum_i U_j[i, b] v[perm[leafoff[j] + i]]
 __global__ void k_restrict_leaf(const double* __restrict__ UT, int KD, int KC, const double* __restrict__ v,
-                                const int* __restrict__ leafoff, const int* __restrict__ perm,
-                                double* __restrict__ out) {
+                                int64_t ldv, const int* __restrict__ leafoff, const int* __restrict__ perm,
+                                double* __restrict__ out, int64_t ldo) {
   __shared__ double xs[64];
+  v += blockIdx.y * ldv;
+  out += blockIdx.y * ldo;
   int j = blockIdx.x;
   int p0 = leafoff[j], nj = leafoff[j + 1] - p0;
   for (int i = threadIdx.x; i < KD; i += blockDim.x) xs[i] = i < nj ? v[perm[p0 + i]] : 0.0;
@@ -152,9 +176,11 @@ __global__ void k_restrict_leaf(const double* __restrict__ UT, int KD, int KC, c
 }
 // v[perm[...]] += sum_b U_j[i, b] e[j*KC + b]
 __global__ void k_prolong_leaf(const double* __restrict__ U, int KD, int KC, const double* __restrict__ e,
-                               const int* __restrict__ leafoff, const int* __restrict__ perm,
-                               double* __restrict__ v) {
+                               int64_t lde, const int* __restrict__ leafoff, const int* __restrict__ perm,
+                               double* __restrict__ v, int64_t ldv) {
   __shared__ double es[64];
+  e += blockIdx.y * lde;
+  v += blockIdx.y * ldv;
   int j = blockIdx.x;
   for (int b = threadIdx.x; b < KC; b += blockDim.x) es[b] = e[(int64_t)j * KC + b];
   __syncthreads();
@@ -167,9 +193,11 @@ __global__ void k_prolong_leaf(const double* __restrict__ U, int KD, int KC, con
   }
 }
 // out[p*KC + b] = sum_{c in children(p)} sum_a E'_c[a, b] v[c*KC + a]
-__global__ void k_restrict(const double* __restrict__ ET, int KC, const double* __restrict__ v,
-                           double* __restrict__ out) {
+__global__ void k_restrict(const double* __restrict__ ET, int KC, const double* __restrict__ v, int64_t ldv,
+                           double* __restrict__ out, int64_t ldo) {
   __shared__ double xs[128];
+  v += blockIdx.y * ldv;
+  out += blockIdx.y * ldo;
   int p = blockIdx.x;
   for (int i = threadIdx.x; i < 2 * KC; i += blockDim.x) xs[i] = v[(int64_t)2 * p * KC + i];
   __syncthreads();
@@ -183,9 +211,11 @@ __global__ void k_restrict(const double* __restrict__ ET, int KC, const double* 
   }
 }
 // v[c*KC + a] += sum_b E'_c[a, b] e[parent*KC + b]
-__global__ void k_prolong(const double* __restrict__ E, int KC, const double* __restrict__ e,
-                          double* __restrict__ v) {
+__global__ void k_prolong(const double* __restrict__ E, int KC, const double* __restrict__ e, int64_t lde,
+                          double* __restrict__ v, int64_t ldv) {
   __shared__ double es[64];
+  e += blockIdx.y * lde;
+  v += blockIdx.y * ldv;
   int c = blockIdx.x;
   for (int b = threadIdx.x; b < KC; b += blockDim.x) es[b] = e[(int64_t)(c >> 1) * KC + b];
   __syncthreads();
@@ -206,155 +236,246 @@ int64_t level_size(const Matrix& M, int i) {
 struct Work {
   double *r[40], *et[40];
   double *cr, *cp, *cq, *t1, *t2;
-  double *pa, *pb;
+  double *pa, *pb, *scal;
   CGState* st;
 };
 
+// Multigrid workspaces for NRMAX columns, allocated on first use.
 static Work work(Matrix& M) {
   Work W{};
-  if (!M.wvec.p) {
-    size_t tot = 0;
-    for (int i = 1; i <= M.lev; ++i) tot += 2 * (size_t)level_size(M, i);
-    size_t nmax = 0;
-    for (int i = 1; i <= M.lev; ++i) nmax = std::max(nmax, (size_t)level_size(M, i));
-    tot += 5 * nmax;
-    M.wvec.bytes = sizeof(double) * tot;
-    M.wvec.p = M.alloc(M.wvec.bytes);
-    M.wred.bytes = sizeof(double) * 2 * NPART + sizeof(CGState) + 64;
-    M.wred.p = M.alloc(M.wred.bytes);
-  }
-  double* p = (double*)M.wvec.p;
-  size_t nmax = 0;
+  size_t tot = 0, nmax = 0;
   for (int i = 1; i <= M.lev; ++i) {
-    W.r[i] = p;
-    p += level_size(M, i);
-    W.et[i] = p;
-    p += level_size(M, i);
+    tot += 2 * (size_t)level_size(M, i);
     nmax = std::max(nmax, (size_t)level_size(M, i));
   }
-  W.cr = p; p += nmax;
-  W.cp = p; p += nmax;
-  W.cq = p; p += nmax;
-  W.t1 = p; p += nmax;
-  W.t2 = p; p += nmax;
+  tot += 5 * nmax;
+  if (!M.wvec.p) {
+    M.wvec.bytes = sizeof(double) * tot * NRMAX;
+    M.wvec.p = M.alloc(M.wvec.bytes);
+    M.wred.bytes = sizeof(double) * (2 * NPART + 8) * NRMAX + sizeof(CGState) * NRMAX + 64;
+    M.wred.p = M.alloc(M.wred.bytes);
+    M.wfcg.bytes = sizeof(double) * 4 * (size_t)M.n * NRMAX;   // flexible-CG directions
+    M.wfcg.p = M.alloc(M.wfcg.bytes);
+  }
+  double* p = (double*)M.wvec.p;
+  for (int i = 1; i <= M.lev; ++i) {
+    W.r[i] = p;
+    p += level_size(M, i) * NRMAX;
+    W.et[i] = p;
+    p += level_size(M, i) * NRMAX;
+  }
+  W.cr = p; p += nmax * NRMAX;
+  W.cp = p; p += nmax * NRMAX;
+  W.cq = p; p += nmax * NRMAX;
+  W.t1 = p; p += nmax * NRMAX;
+  W.t2 = p; p += nmax * NRMAX;
   W.pa = (double*)M.wred.p;
-  W.pb = W.pa + NPART;
-  W.st = (CGState*)(W.pb + NPART);
+  W.pb = W.pa + NPART * NRMAX;
+  W.scal = W.pb + NPART * NRMAX;
+  W.st = (CGState*)(W.scal + 8 * NRMAX);
   return W;
 }
 
-static void dot_part(const double* a, const double* b, int64_t n, double* part, cudaStream_t s) {
-  { k_dot_part<<<part_grid(n), 256, 0, s>>>(a, b, n, part); ::h2mg::count_launch(); }
+// Allocated with the matrix, so that solves on any stream find them ready.
+void alloc_solve_workspace(Matrix& M) { work(M); }
+
+static void dot_part(const double* a, const double* b, int64_t n, int64_t ld, int nr, double* part,
+                     cudaStream_t s) {
+  { k_dot_part<<<dim3(part_grid(n), nr), 256, 0, s>>>(a, b, n, ld, part); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
 }
 
-// n CG iterations on A_i x = f from x0 (nullptr: zero). x receives the iterate; r (if
-// not null) the recurrence residual. Follows Hestenes-Stiefel with the breakdown
-// guard p^T A p <= 0 and the stop r^T r <= (1e-30 |f|)^2.
-void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n, double* x,
-            double* r, cudaStream_t s) {
+// n CG iterations on A_i X = F from X0 (nullptr: zero) for nr columns of length N_i.
+// X receives the iterates; R (if not null) the recurrence residuals. Hestenes-Stiefel
+// with, per column, the breakdown guard p^T A p <= 0 and the stop r^T r <= (1e-30 |f|)^2.
+void smooth_multi(Matrix& M, int i, bool f32, const double* f, const double* x0, int n, double* x, double* r,
+                  int nr, cudaStream_t s) {
+  H2_REQUIRE(nr >= 1 && nr <= NRMAX, H2MG_ERR_INVALID_ARG, "too many columns for one smoother call");
   Work W = work(M);
-  int64_t N = level_size(M, i);
+  const int64_t N = level_size(M, i), tot = N * nr;
   double* rr = r ? r : W.cr;
-  int g = vec_grid(N);
+  const int g = vec_grid(N), np = part_grid(N);
   if (x0 == nullptr) {
-    H2_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
-    H2_CUDA(cudaMemcpyAsync(rr, f, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    H2_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * tot, s));
+    H2_CUDA(cudaMemcpyAsync(rr, f, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
   } else {
-    if (x != x0) H2_CUDA(cudaMemcpyAsync(x, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-    apply_level(M, i, f32, x, W.cq, s);
-    { k_sub<<<g, 256, 0, s>>>(f, W.cq, rr, N); ::h2mg::count_launch(); }
+    if (x != x0) H2_CUDA(cudaMemcpyAsync(x, x0, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+    apply_level_multi(M, i, f32, x, N, W.cq, N, nr, s);
+    { k_sub<<<vec_grid(tot), 256, 0, s>>>(f, W.cq, rr, tot); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
-  H2_CUDA(cudaMemcpyAsync(W.cp, rr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-  dot_part(rr, rr, N, W.pa, s);
-  dot_part(f, f, N, W.pb, s);
-  { k_cg_init<<<1, 32, 0, s>>>(W.pa, part_grid(N), W.pb, part_grid(N), W.st); ::h2mg::count_launch(); }
+  H2_CUDA(cudaMemcpyAsync(W.cp, rr, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+  dot_part(rr, rr, N, N, nr, W.pa, s);
+  dot_part(f, f, N, N, nr, W.pb, s);
+  { k_cg_init<<<1, 32, 0, s>>>(W.pa, W.pb, np, nr, W.st); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
   for (int it = 0; it < n; ++it) {
     const int par = it & 1;
-    apply_level(M, i, f32, W.cp, W.cq, s);
-    dot_part(W.cp, W.cq, N, W.pa, s);
-    { k_cg_update<<<part_grid(N), 256, 0, s>>>(x, rr, W.cp, W.cq, N, W.st, W.pa, part_grid(N), par, W.pb); ::h2mg::count_launch(); }
+    apply_level_multi(M, i, f32, W.cp, N, W.cq, N, nr, s);
+    dot_part(W.cp, W.cq, N, N, nr, W.pa, s);
+    { k_cg_update<<<dim3(np, nr), 256, 0, s>>>(x, rr, W.cp, W.cq, N, N, W.st, W.pa, np, par, W.pb); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
-    { k_cg_p<<<g, 256, 0, s>>>(W.cp, rr, N, W.st, W.pb, part_grid(N), par); ::h2mg::count_launch(); }
+    { k_cg_p<<<dim3(g, nr), 256, 0, s>>>(W.cp, rr, N, N, W.st, W.pb, np, par); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
+}
+
+void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n, double* x, double* r,
+            cudaStream_t s) {
+  smooth_multi(M, i, f32, f, x0, n, x, r, 1, s);
+}
+
+static void restrict_multi(Matrix& M, int i, const double* v, double* out, int nr, cudaStream_t s) {
+  const int KC = M.KC, KD = M.KD, L = M.L;
+  const int64_t nf = level_size(M, i), nc = level_size(M, i + 1);
+  if (i == 1) {
+    { k_restrict_leaf<<<dim3(1 << L, nr), std::max(KC, 32), 0, s>>>(M.d_UT, KD, KC, v, nf, M.d_leafoff, M.d_perm,
+                                                                    out, nc); ::h2mg::count_launch(); }
+  } else {
+    int m = L - i + 2;
+    { k_restrict<<<dim3(1 << (m - 1), nr), std::max(KC, 32), 0, s>>>(M.d_ET + (size_t)M.slot0(m) * KC * KC, KC, v,
+                                                                     nf, out, nc); ::h2mg::count_launch(); }
+  }
+  H2_LAUNCH_CHECK();
+}
+
+static void prolong_add_multi(Matrix& M, int i, const double* e, double* out, int nr, cudaStream_t s) {
+  const int KC = M.KC, KD = M.KD, L = M.L;
+  const int64_t nf = level_size(M, i), nc = level_size(M, i + 1);
+  if (i == 1) {
+    { k_prolong_leaf<<<dim3(1 << L, nr), std::max(KD, 32), 0, s>>>(M.d_U, KD, KC, e, nc, M.d_leafoff, M.d_perm,
+                                                                   out, nf); ::h2mg::count_launch(); }
+  } else {
+    int m = L - i + 2;
+    { k_prolong<<<dim3(1 << m, nr), std::max(KC, 32), 0, s>>>(M.d_E + (size_t)M.slot0(m) * KC * KC, KC, e, nc,
+                                                              out, nf); ::h2mg::count_launch(); }
+  }
+  H2_LAUNCH_CHECK();
 }
 
 void restrict_level(Matrix& M, int i, const double* v, double* out, cudaStream_t s) {
-  const int KC = M.KC, KD = M.KD, L = M.L;
-  if (i == 1) {
-    { k_restrict_leaf<<<1 << L, std::max(KC, 32), 0, s>>>(M.d_UT, KD, KC, v, M.d_leafoff, M.d_perm, out); ::h2mg::count_launch(); }
-  } else {
-    int m = L - i + 2;
-    { k_restrict<<<1 << (m - 1), std::max(KC, 32), 0, s>>>(M.d_ET + (size_t)M.slot0(m) * KC * KC, KC, v, out); ::h2mg::count_launch(); }
-  }
-  H2_LAUNCH_CHECK();
+  restrict_multi(M, i, v, out, 1, s);
 }
-
 void prolong_add(Matrix& M, int i, const double* e, double* out, cudaStream_t s) {
-  const int KC = M.KC, KD = M.KD, L = M.L;
-  if (i == 1) {
-    { k_prolong_leaf<<<1 << L, std::max(KD, 32), 0, s>>>(M.d_U, KD, KC, e, M.d_leafoff, M.d_perm, out); ::h2mg::count_launch(); }
-  } else {
-    int m = L - i + 2;
-    { k_prolong<<<1 << m, std::max(KC, 32), 0, s>>>(M.d_E + (size_t)M.slot0(m) * KC * KC, KC, e, out); ::h2mg::count_launch(); }
-  }
-  H2_LAUNCH_CHECK();
+  prolong_add_multi(M, i, e, out, 1, s);
 }
 
-// One V-cycle of Algorithm 1: x_out = x0 + e_1 given r1 = b - A x0.
-void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double* r1, double* xout,
-            cudaStream_t s) {
+// e_1 of one V-cycle of Algorithm 1 for nr columns of r_1 (n x nr, leading
+// dimension n), into the level-1 error buffer W.et[1]. No host synchronisation and no
+// allocation: the sequence can be captured into a CUDA graph.
+static void vcycle_core(Matrix& M, const h2mg_solve_opts& o, const double* r1, int nr, cudaStream_t s) {
+  H2_REQUIRE(nr >= 1 && nr <= NRMAX, H2MG_ERR_INVALID_ARG, "too many columns for one V-cycle");
   Work W = work(M);
   const bool f32 = o.precision == H2MG_PREC_MIXED_F32;
   const int l = M.lev;
-  int64_t n1 = M.n;
   if (l == 1) {
-    coarse_solve(M, r1, W.et[1], s);
-  } else {
-    const double* ri = r1;
-    for (int i = 1; i < l; ++i) {
-      int ni = (i == 1) ? o.n_f : o.n_c;
-      int64_t N = level_size(M, i);
-      smooth(M, i, f32, ri, nullptr, ni, W.et[i], W.cr, s);        // e~_i = Iter(A_i, r_i, 0)
-      const double* res = W.cr;                                      // r_i - A_i e~_i (recurrence)
-      if (o.explicit_restrict_residual) {
-        apply_level(M, i, f32, W.et[i], W.cq, s);
-        { k_sub<<<vec_grid(N), 256, 0, s>>>(ri, W.cq, W.cr, N); ::h2mg::count_launch(); }
-        H2_LAUNCH_CHECK();
-      }
-      restrict_level(M, i, res, W.r[i + 1], s);                      // r_{i+1} = U_i^T (...)
-      if (i > 1) {
-        // keep r_i: the up-sweep smooths against it again
-      }
-      ri = W.r[i + 1];
-      if (i == 1) {
-        // r_1 is the caller's buffer; nothing to copy
-      }
-    }
-    coarse_solve(M, W.r[l], W.et[l], s);                             // e_l = dir_sol(A_l, r_l)
-    for (int i = l - 1; i >= 1; --i) {
-      int ni = (i == 1) ? o.n_f : o.n_c;
-      prolong_add(M, i, W.et[i + 1], W.et[i], s);                    // e~_i += V_i^T e_{i+1}
-      const double* fi = (i == 1) ? r1 : W.r[i];
-      smooth(M, i, f32, fi, W.et[i], ni, W.et[i], nullptr, s);       // e_i = Iter(A_i, r_i, e~_i)
-    }
+    coarse_solve_multi(M, r1, W.et[1], nr, s);
+    return;
   }
-  { k_add<<<vec_grid(n1), 256, 0, s>>>(x0, W.et[1], xout, n1); ::h2mg::count_launch(); }         // x* = x0 + e_1
+  const double* ri = r1;
+  for (int i = 1; i < l; ++i) {
+    const int ni = (i == 1) ? o.n_f : o.n_c;
+    const int64_t N = level_size(M, i);
+    smooth_multi(M, i, f32, ri, nullptr, ni, W.et[i], W.cr, nr, s);   // e~_i = Iter(A_i, r_i, 0)
+    if (o.explicit_restrict_residual) {                              // r_i - A_i e~_i, explicitly
+      apply_level_multi(M, i, f32, W.et[i], N, W.cq, N, nr, s);
+      { k_sub<<<vec_grid(N * nr), 256, 0, s>>>(ri, W.cq, W.cr, N * nr); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+    }
+    restrict_multi(M, i, W.cr, W.r[i + 1], nr, s);                   // r_{i+1} = U_i^T (r_i - A_i e~_i)
+    ri = W.r[i + 1];
+  }
+  coarse_solve_multi(M, W.r[l], W.et[l], nr, s);                     // e_l = dir_sol(A_l, r_l)
+  for (int i = l - 1; i >= 1; --i) {
+    const int ni = (i == 1) ? o.n_f : o.n_c;
+    prolong_add_multi(M, i, W.et[i + 1], W.et[i], nr, s);            // e~_i += V_i^T e_{i+1}
+    const double* fi = (i == 1) ? r1 : W.r[i];
+    smooth_multi(M, i, f32, fi, W.et[i], ni, W.et[i], nullptr, nr, s);   // e_i = Iter(A_i, r_i, e~_i)
+  }
+}
+
+// One V-cycle for nr columns: x_out = x0 + e_1 given r1 = b - A x0 (x0, r1 and x_out
+// are n x nr with leading dimension n; x_out may be x0).
+void vcycle_multi(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double* r1, double* xout, int nr,
+                  cudaStream_t s) {
+  Work W = work(M);
+  vcycle_core(M, o, r1, nr, s);
+  const int64_t n1 = M.n;
+  { k_add<<<vec_grid(n1 * nr), 256, 0, s>>>(x0, W.et[1], xout, n1 * nr); ::h2mg::count_launch(); }   // x* = x0 + e_1
   H2_LAUNCH_CHECK();
 }
 
-static double norm2(Matrix& M, const double* v, int64_t n, cudaStream_t s) {
+void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double* r1, double* xout, cudaStream_t s) {
+  vcycle_multi(M, o, x0, r1, xout, 1, s);
+}
+
+// ----------------------------------------------------------------------------- graphs
+// A V-cycle (vcycle_core on the solve's residual buffer) captured once per solve
+// setting and column count, then replayed with one launch per outer iteration.
+struct GraphEntry {
+  int nr, n_f, n_c, f32, err;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;   // kernels per replay
+};
+struct GraphSet {
+  std::vector<GraphEntry> g;
+};
+
+void destroy_graphs(Matrix& M) {
+  if (M.graphs) {
+    for (auto& e : M.graphs->g)
+      if (e.exec) best_effort(cudaGraphExecDestroy(e.exec), "cudaGraphExecDestroy");
+    delete M.graphs;
+    M.graphs = nullptr;
+  }
+  if (M.cap_stream) {
+    best_effort(cudaStreamDestroy(M.cap_stream), "cudaStreamDestroy (capture)");
+    M.cap_stream = nullptr;
+  }
+}
+
+static const GraphEntry& vcycle_graph(Matrix& M, const h2mg_solve_opts& o, int nr) {
+  if (!M.graphs) M.graphs = new GraphSet();
+  const int f32 = o.precision == H2MG_PREC_MIXED_F32;
+  for (const GraphEntry& e : M.graphs->g)
+    if (e.nr == nr && e.n_f == o.n_f && e.n_c == o.n_c && e.f32 == f32 && e.err == o.explicit_restrict_residual)
+      return e;
+  if (!M.cap_stream) H2_CUDA(cudaStreamCreateWithFlags(&M.cap_stream, cudaStreamNonBlocking));
   Work W = work(M);
-  dot_part(v, v, n, W.pa, s);
-  std::vector<double> h(part_grid(n));
-  H2_CUDA(cudaMemcpyAsync(h.data(), W.pa, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
-  H2_CUDA(cudaStreamSynchronize(s));
-  double t = 0.0;
-  for (double x : h) t += x;
-  return std::sqrt(t);
+  GraphEntry e{nr, o.n_f, o.n_c, f32, o.explicit_restrict_residual};
+  cudaGraph_t graph = nullptr;
+  const int64_t l0 = h2mg_launch_count();
+  H2_CUDA(cudaStreamBeginCapture(M.cap_stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    vcycle_core(M, o, W.t1, nr, M.cap_stream);
+  } catch (...) {
+    best_effort(cudaStreamEndCapture(M.cap_stream, &graph), "cudaStreamEndCapture (after an error)");
+    if (graph) best_effort(cudaGraphDestroy(graph), "cudaGraphDestroy (after an error)");
+    add_launches(l0 - h2mg_launch_count());
+    throw;
+  }
+  e.launches = h2mg_launch_count() - l0;
+  add_launches(-e.launches);   // captured, not run
+  H2_CUDA(cudaStreamEndCapture(M.cap_stream, &graph));
+  const cudaError_t err = cudaGraphInstantiate(&e.exec, graph, 0);
+  best_effort(cudaGraphDestroy(graph), "cudaGraphDestroy");
+  H2_CUDA(err);
+  M.graphs->g.push_back(e);
+  return M.graphs->g.back();
+}
+
+// e_1 of one V-cycle from the solve's residual buffer W.t1 into W.et[1]: replayed
+// from a captured graph when the options ask for it, launched directly while the
+// block products are being profiled (their events are host-recorded).
+static void vcycle_solve_step(Matrix& M, const h2mg_solve_opts& o, int nr, cudaStream_t s) {
+  Work W = work(M);
+  if (!o.use_graph || M.prof.on) {
+    vcycle_core(M, o, W.t1, nr, s);
+    return;
+  }
+  const GraphEntry& e = vcycle_graph(M, o, nr);
+  H2_CUDA(cudaGraphLaunch(e.exec, s));
+  add_launches(e.launches);
 }
 
 // x^T y on the device (two-pass deterministic sum), read back to the host.
@@ -364,7 +485,7 @@ double device_dot(const double* a, const double* b, int64_t n, cudaStream_t s) {
   H2_CUDA(cudaMalloc(&part, sizeof(double) * NPART));
   double t = 0.0;
   try {
-    dot_part(a, b, n, part, s);
+    dot_part(a, b, n, n, 1, part, s);
     std::vector<double> h(part_grid(n));
     H2_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaStreamSynchronize(s));
@@ -377,87 +498,121 @@ double device_dot(const double* a, const double* b, int64_t n, cudaStream_t s) {
   return t;
 }
 
-static double dot_host(Matrix& M, const double* a, const double* b, int64_t n, cudaStream_t s) {
+// out[c] = a_c^T b_c for nr columns of length n (leading dimension n), on the host.
+static void dots_host(Matrix& M, const double* a, const double* b, int64_t n, int nr, double* out, cudaStream_t s) {
   Work W = work(M);
-  dot_part(a, b, n, W.pa, s);
-  std::vector<double> h(part_grid(n));
+  dot_part(a, b, n, n, nr, W.pa, s);
+  const int np = part_grid(n);
+  std::vector<double> h((size_t)NPART * nr);
   H2_CUDA(cudaMemcpyAsync(h.data(), W.pa, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
   H2_CUDA(cudaStreamSynchronize(s));
-  double t = 0.0;
-  for (double v : h) t += v;
-  return t;
+  for (int c = 0; c < nr; ++c) {
+    double t = 0.0;
+    for (int i = 0; i < np; ++i) t += h[(size_t)c * NPART + i];
+    out[c] = t;
+  }
 }
 
-// Outer iteration: repeated V-cycles x <- x + V(b - A x) (Sec. 3.3), or flexible CG
-// preconditioned by one V-cycle (the new direction is made A-orthogonal to the
-// previous one because the V-cycle with CG smoothers is a nonlinear map). The
-// residual b - A x is recomputed in float64 before every cycle.
-h2mg_status solve(Matrix& M, const double* b, double* x, const h2mg_solve_opts& o, h2mg_solve_info* info,
-                  cudaStream_t s) {
+// y_c += alpha[c] x_c with the coefficients from the host.
+static void axpy_cols(Matrix& M, const double* alpha, const double* x, double* y, int64_t n, int nr,
+                      cudaStream_t s) {
+  Work W = work(M);
+  H2_CUDA(cudaMemcpyAsync(W.scal, alpha, sizeof(double) * nr, cudaMemcpyHostToDevice, s));
+  { k_axpy_cols<<<dim3(vec_grid(n), nr), 256, 0, s>>>(W.scal, x, y, n, n); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
+}
+
+// Outer iteration for nr columns (b, x: n x nr, leading dimension n): repeated
+// V-cycles x <- x + V(b - A x) (Sec. 3.3), or flexible CG preconditioned by one
+// V-cycle (each new direction is made A-orthogonal to the previous one because the
+// V-cycle with CG smoothers is a nonlinear map). The float64 residual b - A x is
+// recomputed before every cycle; a column that has met the tolerance keeps its x
+// from then on. info[c] receives column c's statistics.
+h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2mg_solve_opts& o,
+                        h2mg_solve_info* info, cudaStream_t s) {
+  H2_REQUIRE(nr >= 1 && nr <= NRMAX, H2MG_ERR_INVALID_ARG, "too many columns for one solve");
   Work W = work(M);
   const int64_t n = M.n;
   auto t0 = std::chrono::steady_clock::now();
-  double nb = norm2(M, b, n, s);
-  H2_REQUIRE(std::isfinite(nb), H2MG_ERR_NAN, "right-hand side is not finite");
-  h2mg_solve_info loc{};
-  h2mg_status st = H2MG_ERR_NOT_CONVERGED;
+  double nb[NRMAX], rel[NRMAX], alpha[NRMAX], beta[NRMAX], d1[NRMAX], d2[NRMAX];
+  bool done[NRMAX];
+  dots_host(M, b, b, n, nr, nb, s);
+  for (int c = 0; c < nr; ++c) {
+    H2_REQUIRE(std::isfinite(nb[c]), H2MG_ERR_NAN, "right-hand side is not finite");
+    nb[c] = std::sqrt(nb[c]);
+    done[c] = false;
+    info[c] = h2mg_solve_info{};
+  }
   double* r = W.t1;
   const bool fcg = o.outer == H2MG_OUTER_FCG;
-  double* z = nullptr;
-  double *p = nullptr, *q = nullptr, *pp = nullptr, *qp = nullptr;
+  double *z = nullptr, *p = nullptr, *q = nullptr, *pp = nullptr, *qp = nullptr;
   if (fcg) {
-    if (!M.wfcg.p) {
-      M.wfcg.bytes = sizeof(double) * 5 * (size_t)n;
-      M.wfcg.p = M.alloc(M.wfcg.bytes);
-    }
-    z = (double*)M.wfcg.p;
-    p = z + n;
-    q = p + n;
-    pp = q + n;
-    qp = pp + n;
+    p = (double*)M.wfcg.p;
+    q = p + n * NRMAX;
+    pp = q + n * NRMAX;
+    qp = pp + n * NRMAX;
   }
-  int g = vec_grid(n);
+  bool nan = false;
   for (int cyc = 0; cyc <= o.max_cycles; ++cyc) {
-    apply_level(M, 1, false, x, W.t2, s);
-    { k_sub<<<g, 256, 0, s>>>(b, W.t2, r, n); ::h2mg::count_launch(); }
+    apply_level_multi(M, 1, false, x, n, W.t2, n, nr, s);
+    { k_sub<<<vec_grid(n * nr), 256, 0, s>>>(b, W.t2, r, n * nr); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
-    double rel = nb > 0 ? norm2(M, r, n, s) / nb : 0.0;
-    if (cyc < 256) loc.relres_hist[cyc] = rel;
-    loc.cycles = cyc;
-    loc.relres = rel;
-    if (!std::isfinite(rel)) {
-      st = H2MG_ERR_NAN;
-      break;
+    dots_host(M, r, r, n, nr, rel, s);
+    bool all = true;
+    for (int c = 0; c < nr; ++c) {
+      if (done[c]) continue;
+      rel[c] = nb[c] > 0 ? std::sqrt(rel[c]) / nb[c] : 0.0;
+      if (cyc < 256) info[c].relres_hist[cyc] = rel[c];
+      info[c].cycles = cyc;
+      info[c].relres = rel[c];
+      if (!std::isfinite(rel[c])) {
+        nan = true;
+        done[c] = true;
+      } else if (rel[c] <= o.tol) {
+        info[c].converged = 1;
+        done[c] = true;
+      }
+      all = all && done[c];
     }
-    if (rel <= o.tol) {
-      st = H2MG_OK;
-      loc.converged = 1;
-      break;
-    }
-    if (cyc == o.max_cycles) break;
+    if (all || nan || cyc == o.max_cycles) break;
+    vcycle_solve_step(M, o, nr, s);                         // W.et[1] = V(r) from zero
     if (!fcg) {
-      vcycle(M, o, x, r, x, s);
+      // x* = x0 + e_1 (Algorithm 1) for the columns still running
+      for (int c = 0; c < nr; ++c) alpha[c] = done[c] ? 0.0 : 1.0;
+      axpy_cols(M, alpha, W.et[1], x, n, nr, s);
       continue;
     }
-    H2_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
-    vcycle(M, o, z, r, z, s);                                   // z = V(r) from zero
-    if (cyc == 0) {
-      H2_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    } else {
-      double beta = -dot_host(M, z, qp, n, s) / dot_host(M, pp, qp, n, s);
-      H2_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      { k_axpby<<<g, 256, 0, s>>>(beta, pp, 1.0, p, n); ::h2mg::count_launch(); }           // p = z + beta p_prev
-      H2_LAUNCH_CHECK();
+    z = W.et[1];
+    H2_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n * nr, cudaMemcpyDeviceToDevice, s));
+    if (cyc > 0) {
+      dots_host(M, z, qp, n, nr, d1, s);
+      dots_host(M, pp, qp, n, nr, d2, s);
+      for (int c = 0; c < nr; ++c) beta[c] = d2[c] != 0.0 ? -d1[c] / d2[c] : 0.0;
+      axpy_cols(M, beta, pp, p, n, nr, s);                   // p = z + beta p_prev
     }
-    apply_level(M, 1, false, p, q, s);
-    double alpha = dot_host(M, p, r, n, s) / dot_host(M, p, q, n, s);
-    { k_axpby<<<g, 256, 0, s>>>(alpha, p, 1.0, x, n); ::h2mg::count_launch(); }             // x += alpha p
-    H2_LAUNCH_CHECK();
+    apply_level_multi(M, 1, false, p, n, q, n, nr, s);
+    dots_host(M, p, r, n, nr, d1, s);
+    dots_host(M, p, q, n, nr, d2, s);
+    for (int c = 0; c < nr; ++c) alpha[c] = (!done[c] && d2[c] > 0.0) ? d1[c] / d2[c] : 0.0;
+    axpy_cols(M, alpha, p, x, n, nr, s);                     // x += alpha p
     std::swap(p, pp);
     std::swap(q, qp);
   }
   H2_CUDA(cudaStreamSynchronize(s));
-  loc.ms_solve = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h2mg_status st = H2MG_OK;
+  for (int c = 0; c < nr; ++c) {
+    info[c].ms_solve = ms;
+    if (!info[c].converged) st = H2MG_ERR_NOT_CONVERGED;
+  }
+  if (nan) st = H2MG_ERR_NAN;
+  return st;
+}
+
+h2mg_status solve(Matrix& M, const double* b, double* x, const h2mg_solve_opts& o, h2mg_solve_info* info,
+                  cudaStream_t s) {
+  h2mg_solve_info loc;
+  const h2mg_status st = solve_multi(M, b, x, 1, o, &loc, s);
   if (info) *info = loc;
   return st;
 }

@@ -9,7 +9,7 @@ struct TempBuf {
     if (bytes) H2_CUDA(cudaMalloc(&p, bytes));
   }
   ~TempBuf() {
-    if (p) cudaFree(p);
+    if (p) best_effort(cudaFree(p), "cudaFree (sort scratch)");
   }
   template <class T>
   T* as() { return static_cast<T*>(p); }
