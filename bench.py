@@ -27,6 +27,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H2-MG solves/s to 1e-10 rel. residual & H2 matvec GB/s (FP64 vs mixed)"
+# DRAM bytes (read + write) per k_bsgemv launch over every block product of one outer
+# iteration of the 2^17 solve, from ncu (profiles/k_bsgemv_dram_gauss3d_n131072.md);
+# the algorithmic bytes per launch of the same launches were 1.5833e9
+TRAFFIC_PER_LAUNCH = 1.5607e9
 
 
 def parse():
@@ -50,6 +54,10 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=8192)
     ap.add_argument("--no-f64", action="store_true", help="skip the plain float64 comparison solve")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph V-cycle measurement")
+    ap.add_argument("--skip-square", action="store_true",
+                    help="also time the solve with skip_square_levels (no smoothing on square levels)")
+    ap.add_argument("--problems", type=int, default=32,
+                    help="independent perturbed-sphere problems solved together after the timed region (0: skip)")
     ap.add_argument("--batch-rhs", type=int, default=4,
                     help="right-hand sides of the batched solve measured after the timed region (0: skip)")
     return ap.parse_args()
@@ -201,6 +209,50 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def uneven_problems(a, pkg, W, torch, stream):
+    """Independent surface problems of uneven size (perturbed spheres, single-layer
+    kernel, N = 20 m^2 with m from the surface workload's log-uniform list) solved
+    together by h2mg_solve_batched (one graph launch per outer iteration for all
+    V-cycles), against the same problems solved one after another. Timed once each,
+    after one untimed batched solve that captures the graphs."""
+    import numpy as np
+    ms = W.surface_problem_sizes(a.problems)
+    mats, bs = [], []
+    t0 = time.perf_counter()
+    for j, m in enumerate(ms):
+        c, ar, _ = W.perturbed_icosphere(m, j)
+        mats.append(pkg.H2Matrix(torch.from_numpy(c).cuda(), "laplace_sl", weights=torch.from_numpy(ar).cuda(),
+                                 leaf=64, q=4, eta=1.0, with_f32=True))
+        bs.append(torch.from_numpy(W.normal_rhs(c.shape[0], 3 + j)).cuda())
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    kw = dict(tol=a.tol, max_cycles=a.max_cycles, n_f=a.nf, n_c=a.nc, precision=a.precision, outer=a.outer)
+    pkg.solve_batched(mats, bs, raise_on_fail=False, use_graph=True, **kw)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    xs, infos = pkg.solve_batched(mats, bs, raise_on_fail=False, use_graph=True, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sb = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    for A, bb in zip(mats, bs):
+        A.solve(bb, raise_on_fail=False, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ss = e0.elapsed_time(e1) / 1e3
+    worst = max(float(((bb - A.apply(x)).norm() / bb.norm()).item()) for A, bb, x in zip(mats, bs, xs))
+    n = [20 * m * m for m in ms]
+    out = {"problems": len(ms), "n_min": min(n), "n_max": max(n), "n_total": sum(n),
+           "kernel": "single-layer 1/(4 pi r), panel areas as weights", "build_s": build_s,
+           "s_batched": sb, "problems_per_s": len(ms) / sb, "s_one_by_one": ss,
+           "speedup_vs_one_by_one": ss / sb, "cycles_max": max(i.cycles for i in infos),
+           "converged": all(i.converged for i in infos) and worst <= a.tol * 1.0001, "max_relres": worst}
+    for A in mats:
+        A.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 # --------------------------------------------------------------------------- our arm
 def main():
     a = parse()
@@ -231,6 +283,8 @@ def main():
         Am = pkg.H2Matrix(Xm, "gaussian", length=a.length, nugget=a.nugget, leaf=64, q=4, eta=1.0,
                           storage="f64", with_f32=True)
         xv = torch.randn(a.matvec_n, dtype=torch.float64, device="cuda")
+        if os.environ.get("H2MG_BENCH_REPORT_LAUNCHES"):
+            print(f"launches before the matvec: {pkg.H2Matrix.launch_count()}", file=sys.stderr, flush=True)
         yv = torch.empty_like(xv)
         matvec = {}
         for prec in ("f64", "mixed_f32"):
@@ -334,6 +388,21 @@ def main():
         graph = {"s_per_solve": sg, "solves_per_s": 1.0 / sg, "cycles": ig_.cycles,
                  "converged": bool(ig_.converged), "speedup_vs_direct": (ms / 1e3 / a.steps) / sg}
 
+    # ---- the same solve without smoothing on levels whose restriction is square
+    # (U_1 is 64 x 64 here: A_2 is an orthogonal similarity of A_1), timed once
+    skip = None
+    if a.skip_square:
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        xk_, ik_ = A.solve(b, raise_on_fail=False, skip_square_levels=True, **kw)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        sk = k0.elapsed_time(k1) / 1e3
+        relk = float(((b - A.apply(xk_)).norm() / b.norm()).item())
+        skip = {"s_per_solve": sk, "solves_per_s": 1.0 / sk, "cycles": ik_.cycles,
+                "converged": bool(ik_.converged) and relk <= a.tol * 1.0001, "relres": relk,
+                "speedup_vs_literal": (ms / 1e3 / a.steps) / sk}
+
     # ---- batched form: several right-hand sides solved together (one group of columns
     # shares every block read of every product), timed once
     batched = None
@@ -341,6 +410,8 @@ def main():
         Bm = torch.from_numpy(np.ascontiguousarray(W.normal_rhs(a.n, 2, a.batch_rhs))).cuda() \
             if a.batch_rhs > 1 else b[:, None].clone()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if os.environ.get("H2MG_BENCH_REPORT_LAUNCHES"):
+            print(f"launches before the batched solve: {pkg.H2Matrix.launch_count()}", file=sys.stderr, flush=True)
         g0.record(stream)
         Xb, ib = A.solve(Bm, raise_on_fail=False, **kw)
         ib = ib if isinstance(ib, list) else [ib]
@@ -355,12 +426,17 @@ def main():
                    "speedup_vs_single_rhs": (a.batch_rhs / sb) / (a.steps / (ms / 1e3)),
                    "precision": a.precision}
     A.close()
+    del A
+    torch.cuda.empty_cache()
+
+    problems = uneven_problems(a, pkg, W, torch, stream) if a.problems > 0 else None
 
     kernel_gbs = kby / kms / 1e6 if kms > 0 else 0.0
     bound = "hbm"
     peak = pk["hbm_gbs"]
     roof = {"bound": bound, "achieved": kernel_gbs, "peak": peak, "unit": "GB/s",
-            "frac": kernel_gbs / peak, "traffic": None,
+            "frac": kernel_gbs / peak, "traffic": TRAFFIC_PER_LAUNCH if a.n == 1 << 17 else None,
+            "traffic_source": "profiles/k_bsgemv_dram_gauss3d_n131072.md (ncu, one outer iteration)",
             "kernel": "k_bsgemv (symmetric block-sparse product)", "launches": nk,
             "bytes_per_launch": kby / max(nk, 1), "ms_per_launch": kms / max(nk, 1),
             "peak_source": f"{pk_kind} hbm_gbs"}
@@ -376,7 +452,8 @@ def main():
                        "l2": "inputs larger than L2 (stored blocks)", "build_s": build_s,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "cycles": cycles, "converged": converged, "relres": infos[-1][2], "relres_check": res_check,
-            "matvec": matvec, "f64_solve": f64, "graph": graph, "batched": batched, "roofline": roof, "gpu_launches": launches,
+            "matvec": matvec, "f64_solve": f64, "graph": graph, "skip_square_levels": skip, "batched": batched,
+            "problems": problems, "roofline": roof, "gpu_launches": launches,
             "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 16 * a.n,
                     "d2h_bytes_per_step": 8 * a.n},
             "clocks": clk.summary()}

@@ -54,13 +54,17 @@ typedef enum {
     H2MG_K_GAUSSIAN = 0,      /* exp(-r^2 / length^2)     (Sec. 4.1 with sigma = length^2) */
     H2MG_K_EXPONENTIAL = 1,   /* exp(-r / length)          (Sec. 4.2 with sigma = length)   */
     H2MG_K_MATERN32 = 2,      /* (1 + sqrt3 r/length) exp(-sqrt3 r/length)                 */
-    H2MG_K_LAPLACE_SL = 3,    /* 1 / (4 pi r)  single-layer potential (Sec. 4.3); needs diag */
+    H2MG_K_LAPLACE_SL = 3,    /* 1 / (4 pi r)  single-layer potential (Sec. 4.3); needs weights
+                                 (panel areas a_i) or diag                                  */
     H2MG_K_POLY = 4,          /* (1 + x.y)^degree  (test kernel: exact in H2 if degree < q)  */
     H2MG_K_DMATERN32_DL = 5   /* d/dlength of the Matern-3/2 kernel: (3 r^2/l^3) exp(-sqrt3 r/l) */
 } h2mg_kernel_kind;
 
 /* A_ij = sqrt(w_i) k(x_i, x_j) sqrt(w_j) for i != j;
- * A_ii = (diag ? diag[i] : w_i k(x_i, x_i)) + nugget       (eqs. a_gau/a_exp: 1 + c). */
+ * A_ii = (diag ? diag[i] : w_i k(x_i, x_i)) + nugget       (eqs. a_gau/a_exp: 1 + c).
+ * LAPLACE_SL without diag: A_ii = sqrt(w_i / pi) / 2, the potential at the centre of a
+ * flat disk of area w_i carrying unit density (the panel's self-interaction, Sec. 4.3,
+ * in the symmetric scaling of the off-diagonal entries). */
 typedef struct {
     int kind;                 /* h2mg_kernel_kind */
     double length;            /* length scale, > 0 (ignored by POLY and LAPLACE_SL) */
@@ -106,6 +110,12 @@ typedef struct {
                                        While h2mg_profile is enabled the V-cycle is
                                        launched directly (profiling events are recorded
                                        from the host around each block product) */
+    int skip_square_levels;         /* 1: no smoothing on a level i >= 2 whose restriction
+                                       U_{i-1} is square (every leaf, or every cluster of
+                                       level m(i), has as many basis columns as rows), so
+                                       that A_i is an orthogonal similarity of A_{i-1} and
+                                       not a coarser operator: the V-cycle passes the
+                                       residual through it. 0: Algorithm 1 literally */
 } h2mg_solve_opts;
 
 typedef struct {
@@ -146,6 +156,18 @@ h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int6
  * residual is not finite. */
 h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int64_t ld,
                        const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream);
+
+/* Solve nprob independent problems A[p] x[p] = b[p] (one column each, each matrix
+ * built separately with its own size, kernel and tree; no matrix twice) with H2-MG,
+ * together: every outer iteration computes all residuals and reads all their norms
+ * with one synchronisation, runs the V-cycles of all unconverged problems and then
+ * the outer updates. With o->use_graph the V-cycles are one launch of a CUDA graph
+ * with one branch per problem (each problem's captured V-cycle), so the kernels of
+ * small problems run concurrently. b[p], x[p]: n_p entries, host or device; x[p]
+ * holds the initial guess. info: nprob structs, one per problem. Same statuses as
+ * h2mg_solve (NOT_CONVERGED if any problem did not converge). */
+h2mg_status h2mg_solve_batched(int nprob, const h2mg_matrix* A, const double* const* b, double* const* x,
+                               const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream);
 
 /* Build the H2 matrix of another kernel on the same points with the same cluster
  * tree, block partition, Chebyshev nodes and orthonormalisation factors as A

@@ -84,10 +84,18 @@ def diag_value(kind: str, X: np.ndarray, weights, diag, nugget: float, length: f
 
 
 def surface_diag(areas: np.ndarray) -> np.ndarray:
-    """Self-interaction of a flat panel of area a for the single-layer kernel with
-    symmetric weights: a * sqrt(a/pi) / 2 (the workload's diagonal)."""
+    """Diagonal of the single-layer matrix (Sec. 4.3) in the symmetric scaling
+    A_ij = sqrt(a_i a_j) / (4 pi |c_i - c_j|): the panel's self-interaction, taken as
+    the potential at the centre of a flat disk of the panel's area a carrying unit
+    density, int_disk dA / (4 pi |x - c|) = R / 2 with R = sqrt(a / pi).
+
+    It has the units of the off-diagonal entries (a length). The paper's own choice,
+    w_i / (4 pi R_i) with R_i the mean centroid-vertex distance, is about half of it;
+    on the perturbed spheres of the surface workload both it and the formula
+    a sqrt(a/pi)/2 (an extra factor a) leave the matrix indefinite, while this one
+    keeps it positive definite."""
     a = np.asarray(areas, dtype=np.float64)
-    return a * np.sqrt(a / math.pi) / 2.0
+    return np.sqrt(a / math.pi) / 2.0
 
 
 def dense_kernel_matrix(kind: str, X: np.ndarray, length: float = 1.0, nugget: float = 0.0,

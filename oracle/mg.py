@@ -37,6 +37,7 @@ class SolveOpts:
     n_c: int = 40                     # coarse-level CG iterations
     explicit_restrict_residual: bool = False
     coarse_level: int = -1            # -1: natural l = L - t* + 1
+    skip_square_levels: bool = False  # no smoothing where U_{i-1} is square (A_i similar to A_{i-1})
 
 
 @dataclass
@@ -211,17 +212,26 @@ def vcycle(mg: H2MG, x0: np.ndarray, r1: np.ndarray, opts: SolveOpts, ops=None) 
     l = mg.l
     if l == 1:
         return x0 + mg.dir_sol(r1).astype(r1.dtype)
+    def iters(i):
+        # a level whose restriction U_{i-1} is square (N_i = N_{i-1}; the columns are
+        # orthonormal) is an orthogonal similarity of the finer one, not a coarser space
+        if i == 1:
+            return opts.n_f
+        if opts.skip_square_levels and mg.size(i) == mg.size(i - 1):
+            return 0
+        return opts.n_c
+
     r = {1: r1}
     et = {}
     for i in range(1, l):
-        n_i = opts.n_f if i == 1 else opts.n_c
+        n_i = iters(i)
         A = (lambda v, i=i: ops.apply(i, v))
         et[i], rho = cg(A, r[i], None, n_i)
         res = r[i] - A(et[i]) if opts.explicit_restrict_residual else rho
         r[i + 1] = ops.restrict(i, res)
     e = mg.dir_sol(r[l]).astype(r1.dtype)
     for i in range(l - 1, 0, -1):
-        n_i = opts.n_f if i == 1 else opts.n_c
+        n_i = iters(i)
         A = (lambda v, i=i: ops.apply(i, v))
         et[i] = et[i] + ops.prolong(i, e)
         e, _ = cg(A, r[i], et[i], n_i)

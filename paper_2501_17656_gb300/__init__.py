@@ -36,7 +36,7 @@ X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5)
 EXPORTED = ["h2mg_build", "h2mg_apply", "h2mg_solve", "h2mg_destroy", "h2mg_error_string",
             "h2mg_last_error", "h2mg_query", "h2mg_export", "h2mg_apply_level",
             "h2mg_coarse_solve", "h2mg_smooth", "h2mg_vcycle", "h2mg_launch_count", "h2mg_profile",
-            "h2mg_transfer", "h2mg_apply_noalloc", "h2mg_build_sibling", "h2mg_dot"]
+            "h2mg_transfer", "h2mg_apply_noalloc", "h2mg_build_sibling", "h2mg_dot", "h2mg_solve_batched"]
 
 
 class H2MGError(RuntimeError):
@@ -60,7 +60,7 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("n_f", ctypes.c_int),
                 ("n_c", ctypes.c_int), ("precision", ctypes.c_int),
                 ("explicit_restrict_residual", ctypes.c_int), ("outer", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("skip_square_levels", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -107,6 +107,8 @@ def load_library(build_if_missing: bool = False):
     lib.h2mg_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.h2mg_build_sibling.argtypes = [vp, ctypes.POINTER(_Kernel), vp, ctypes.POINTER(vp)]
     lib.h2mg_dot.argtypes = [vp, vp, i64, ctypes.POINTER(cd), vp]
+    lib.h2mg_solve_batched.argtypes = [ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.h2mg_profile.argtypes = [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(cd), ctypes.POINTER(cd)]
     for name in EXPORTED:
         if name not in ("h2mg_error_string", "h2mg_last_error", "h2mg_launch_count"):
@@ -326,9 +328,10 @@ class H2Matrix:
 
     @staticmethod
     def _opts(tol=1e-10, max_cycles=100, n_f=1, n_c=40, precision="f64", explicit_restrict_residual=False,
-              outer="vcycle", use_graph=False):
+              outer="vcycle", use_graph=False, skip_square_levels=False):
         return _SolveOpts(float(tol), int(max_cycles), int(n_f), int(n_c), PRECISION[precision],
-                          int(bool(explicit_restrict_residual)), OUTER[outer], int(bool(use_graph)))
+                          int(bool(explicit_restrict_residual)), OUTER[outer], int(bool(use_graph)),
+                          int(bool(skip_square_levels)))
 
     def vcycle(self, x0, r1, **kw):
         x = _like(x0, self.n)
@@ -403,3 +406,23 @@ class MaternLoss:
                         torch.tensor(gv * ds, dtype=torch.float64, device=dev))
 
         return _Fn.apply(y, b, length, nugget)
+
+
+def solve_batched(mats, bs, xs=None, raise_on_fail: bool = True, **kw):
+    """Solve independent problems mats[p] x_p = bs[p] together (h2mg_solve_batched):
+    the V-cycles of all problems run from one graph launch per outer iteration when
+    ``use_graph=True``. Returns (xs, [SolveInfo per problem])."""
+    P = len(mats)
+    if xs is None:
+        xs = [_like(b, int(b.shape[0])) for b in bs]
+    arr = ctypes.c_void_p * P
+    hs = arr(*[m._h.value for m in mats])
+    bp = arr(*[_ptr(b) for b in bs])
+    xp = arr(*[_ptr(x) for x in xs])
+    o = H2Matrix._opts(**kw)
+    infos = (SolveInfo * P)()
+    lib = load_library()
+    st = lib.h2mg_solve_batched(P, hs, bp, xp, ctypes.byref(o), infos, _stream())
+    if st != 0 and (raise_on_fail or st not in (5,)):
+        _check(st)
+    return xs, list(infos)

@@ -106,6 +106,22 @@ struct Ar<FMT_F32> {
   __device__ static vec_t from_d(double v) { return __double2float_rn(v); }
 };
 
+// NR consecutive elements from shared memory, as one vector load where the row is 8
+// or 16 bytes (rows are aligned to their size).
+template <class T, int NR>
+__device__ __forceinline__ void load_row(const T* p, T* out) {
+  if constexpr (sizeof(T) * NR == 16) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    memcpy(out, &v, 16);
+  } else if constexpr (sizeof(T) * NR == 8) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    memcpy(out, &v, 8);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) out[j] = p[j];
+  }
+}
+
 // ----------------------------------------------------------------------------- block GEMV
 // One CTA (8 warps) per block row t of a symmetric upper-stored block operator:
 // yrow[t] += sum_e B_e x_col(e) and, for every off-diagonal entry e = (t, s),
@@ -115,8 +131,22 @@ struct Ar<FMT_F32> {
 // operator has few rows, each row is split over `split` CTAs (strided entries).
 // NR right-hand sides share every block read: vectors are interleaved, element
 // (slot, coefficient, column j) at ((slot * K + coefficient) * NR + j).
+// CTAs per SM the register allocation must allow: the FP32 products are HBM-bound and
+// need the occupancy; the float64 / double-float ones are ALU-bound.
+template <int FMT, int NR>
+constexpr int bsgemv_min_ctas() {
+  return FMT == FMT_F32 ? (NR >= 4 ? 2 : (NR == 2 ? 3 : 4)) : 2;
+}
+
+// Asks the memory system to bring `bytes` (a multiple of 16, 16-byte aligned) from
+// global memory into L2 without waiting: the next block a warp will read streams in
+// while it works on the current one.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int K, int FMT, int NR>
-__global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(256, bsgemv_min_ctas<FMT, NR>()) k_bsgemv(const int* __restrict__ rowptr,
                                                 const int* __restrict__ col,
                                                 const void* const* __restrict__ blk,
                                                 const typename Ar<FMT>::vec_t* __restrict__ x,
@@ -130,23 +160,33 @@ __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
   constexpr int CH = T < LPC ? T : LPC;
   constexpr int V = A::V, P = 8 / V;
   __shared__ acc_t red[8][K * NR];
+  // x of the block row (input of the transposed products), one padding row after
+  // every 8 rows so that the 8 row groups of a warp read distinct banks
+  __shared__ __align__(16) vec_t sxt[(K + K / 8) * NR];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int row = blockIdx.x / split, part = blockIdx.x % split;
   const int rb = 8 * (lane % LPC), cl = lane / LPC;
-  vec_t xt[8][NR];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int j = 0; j < NR; ++j) xt[r][j] = x[((int64_t)row * K + rb + r) * NR + j];
+  for (int i = threadIdx.x; i < K * NR; i += blockDim.x) {
+    const int r = i / NR;
+    sxt[(r + r / 8) * NR + i % NR] = x[(int64_t)row * K * NR + i];
+  }
+  __syncthreads();
+  const vec_t* xt = sxt + (rb + rb / 8) * NR;   // rows rb..rb+7 of this lane
   acc_t ya[8][NR];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
     for (int j = 0; j < NR; ++j) ya[r][j] = A::zero();
   const int e0 = rowptr[row], e1 = rowptr[row + 1];
+  constexpr unsigned kBlockBytes = K * K / V * (unsigned)sizeof(ld_t);   // one stored block
   for (int e = e0 + part * 8 + w; e < e1; e += 8 * split) {
     const int s = col[e];
     const ld_t* B = (const ld_t*)blk[e];
+    // with one column the loads of 32 warps per SM already cover the DRAM latency, and
+    // prefetched blocks would be evicted from L2 before use; with several columns
+    // (fewer resident warps) the prefetch keeps the stream going
+    if constexpr (NR >= 2)
+      if (lane == 0 && e + 8 * split < e1) prefetch_l2_bulk(blk[e + 8 * split], kBlockBytes);
     const vec_t* xs = x + (int64_t)s * K * NR;
     const bool off = (s != row);
 #pragma unroll 1
@@ -168,7 +208,7 @@ __global__ void __launch_bounds__(256) k_bsgemv(const int* __restrict__ rowptr,
           for (int r = 0; r < 8; ++r) A::fma(ya[r][j], m[r], xv);
           acc_t zz = A::zero();
 #pragma unroll
-          for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r][j]);
+          for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r * NR + j]);
           zc[tt][j] = zz;
         }
         if ((t & 3) == 3) {
@@ -741,6 +781,10 @@ static void apply_impl(Matrix& M, int i, const double* x, int64_t ldx, double* y
   if (i == 1) {
     vt* xp = (vt*)(ws ? ws->xp : M.wxp.p);
     yt* yp = (yt*)(ws ? ws->yp : M.wyp.p);
+    // padded slots must read as zero: the buffer is shared by every format and column
+    // count, so whatever an earlier product left there (possibly the halves of float64
+    // values, which as floats can be NaN) is cleared first
+    H2_CUDA(cudaMemsetAsync(xp, 0, sizeof(vt) * (size_t)(1 << L) * KD * NR, s));
     { k_pts_in<FMT, NR><<<ceil_div(M.n, 256), 256, 0, s>>>(x, ldx, M.d_slot_of, M.n, xp); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     if (ts >= 0) {

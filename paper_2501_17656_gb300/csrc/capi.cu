@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 
 #include "internal.h"
@@ -126,7 +127,10 @@ __global__ void k_point_weights(const int* __restrict__ perm, int64_t n, int dim
   int i = perm[p];
   double wi = w ? w[i] : 1.0;
   sw[p] = sqrt(wi);
-  double d = dg ? dg[i] : wi * kernel_self(kp, Xt + p * dim, dim);
+  // single layer without an override: self-potential of a flat disk of area w_i
+  double d = dg ? dg[i]
+                : (kp.kind == H2MG_K_LAPLACE_SL ? 0.5 * sqrt(wi / 3.141592653589793)
+                                                : wi * kernel_self(kp, Xt + p * dim, dim));
   dgo[p] = d + kp.nugget;
 }
 
@@ -266,8 +270,8 @@ h2mg_status h2mg_build(const double* points, int64_t n, int dim, const h2mg_kern
                H2MG_ERR_INVALID_ARG, "length must be > 0");
     H2_REQUIRE(k->kind != H2MG_K_POLY || (k->degree >= 0 && k->degree <= 16), H2MG_ERR_INVALID_ARG,
                "degree must be in [0, 16]");
-    H2_REQUIRE(k->kind != H2MG_K_LAPLACE_SL || k->diag, H2MG_ERR_INVALID_ARG,
-               "the single-layer kernel needs a diagonal override");
+    H2_REQUIRE(k->kind != H2MG_K_LAPLACE_SL || k->diag || k->weights, H2MG_ERR_INVALID_ARG,
+               "the single-layer kernel needs panel areas (weights) or a diagonal override");
     H2_REQUIRE(std::isfinite(k->nugget), H2MG_ERR_INVALID_ARG, "nugget must be finite");
     auto* h = new h2mg_matrix_s();
     Matrix& M = h->M;
@@ -343,6 +347,41 @@ h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int6
     }
     if (worst != H2MG_OK) set_error(h2mg_error_string(worst));
     return worst;
+  });
+}
+
+h2mg_status h2mg_solve_batched(int nprob, const h2mg_matrix* A, const double* const* b, double* const* x,
+                               const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(nprob >= 1 && A && b && x && o && info, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    H2_REQUIRE(o->max_cycles >= 0 && o->n_f >= 0 && o->n_c >= 0 && o->tol >= 0, H2MG_ERR_INVALID_ARG,
+               "bad solve options");
+    std::vector<Matrix*> Ms(nprob);
+    for (int p = 0; p < nprob; ++p) {
+      H2_REQUIRE(A[p] && b[p] && x[p], H2MG_ERR_INVALID_ARG, "null pointer argument");
+      Matrix& M = A[p]->M;
+      H2_REQUIRE(o->precision == H2MG_PREC_F64 || (o->precision == H2MG_PREC_MIXED_F32 && M.with_f32),
+                 H2MG_ERR_INVALID_ARG, "mixed precision needs matrices built with_f32");
+      H2_REQUIRE(!M.apply_only, H2MG_ERR_INVALID_ARG, "matrix was built for products only");
+      for (int q = 0; q < p; ++q)
+        H2_REQUIRE(A[q] != A[p], H2MG_ERR_INVALID_ARG, "a matrix appears twice (use nrhs columns instead)");
+      if (!M.coarse_ok) throw Error{H2MG_ERR_NOT_SPD, "the coarsest operator of a problem is not positive definite"};
+      Ms[p] = &M;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<std::unique_ptr<DevView>> B, X;
+    std::vector<const double*> bd(nprob);
+    std::vector<double*> xd(nprob);
+    for (int p = 0; p < nprob; ++p) {
+      B.emplace_back(new DevView(b[p], Ms[p]->n, true, s));
+      X.emplace_back(new DevView(x[p], Ms[p]->n, true, s));
+      bd[p] = B.back()->d;
+      xd[p] = X.back()->d;
+    }
+    const h2mg_status st = solve_batched(Ms, bd.data(), xd.data(), *o, info, s);
+    for (int p = 0; p < nprob; ++p) X[p]->copy_out(x[p], Ms[p]->n, s);
+    if (st != H2MG_OK) set_error(h2mg_error_string(st));
+    return st;
   });
 }
 

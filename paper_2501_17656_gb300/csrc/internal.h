@@ -176,6 +176,8 @@ void vcycle_multi(Matrix& M, const h2mg_solve_opts& o, const double* x0, const d
                   cudaStream_t s);
 h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2mg_solve_opts& o,
                         h2mg_solve_info* info, cudaStream_t s);
+h2mg_status solve_batched(const std::vector<Matrix*>& Ms, const double* const* b, double* const* x,
+                          const h2mg_solve_opts& o, h2mg_solve_info* info, cudaStream_t s);
 int64_t level_size(const Matrix& M, int i);
 double device_dot(const double* a, const double* b, int64_t n, cudaStream_t s);
 

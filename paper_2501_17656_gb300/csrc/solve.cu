@@ -295,9 +295,14 @@ void smooth_multi(Matrix& M, int i, bool f32, const double* f, const double* x0,
   const int64_t N = level_size(M, i), tot = N * nr;
   double* rr = r ? r : W.cr;
   const int g = vec_grid(N), np = part_grid(N);
+  if (n == 0 && x0 != nullptr && r == nullptr) {   // no iteration, residual not wanted
+    if (x != x0) H2_CUDA(cudaMemcpyAsync(x, x0, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
   if (x0 == nullptr) {
     H2_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * tot, s));
     H2_CUDA(cudaMemcpyAsync(rr, f, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+    if (n == 0) return;
   } else {
     if (x != x0) H2_CUDA(cudaMemcpyAsync(x, x0, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
     apply_level_multi(M, i, f32, x, N, W.cq, N, nr, s);
@@ -360,6 +365,27 @@ void prolong_add(Matrix& M, int i, const double* e, double* out, cudaStream_t s)
   prolong_add_multi(M, i, e, out, 1, s);
 }
 
+// True if the restriction U_{i-1} into level i >= 2 is square: every cluster of tree
+// level m(i) has as many basis columns as rows (points for leaves, the children's
+// ranks above), so A_i = U_{i-1}^T A_{i-1} U_{i-1} is an orthogonal similarity.
+static bool square_level(const Matrix& M, int i) {
+  if (i < 2 || M.tstar < 0) return false;
+  const int m = M.L - i + 2;
+  if (m < M.tstar || m > M.L) return false;
+  for (int c = 0; c < (1 << m); ++c) {
+    const int rank = M.h_rank[M.slot0(m) + c];
+    int rows;
+    if (m == M.L) {
+      rows = M.offsets[M.L][c + 1] - M.offsets[M.L][c];
+    } else {
+      if (m + 1 > M.L) return false;
+      rows = M.h_rank[M.slot0(m + 1) + 2 * c] + M.h_rank[M.slot0(m + 1) + 2 * c + 1];
+    }
+    if (rank != rows) return false;
+  }
+  return true;
+}
+
 // e_1 of one V-cycle of Algorithm 1 for nr columns of r_1 (n x nr, leading
 // dimension n), into the level-1 error buffer W.et[1]. No host synchronisation and no
 // allocation: the sequence can be captured into a CUDA graph.
@@ -372,9 +398,13 @@ static void vcycle_core(Matrix& M, const h2mg_solve_opts& o, const double* r1, i
     coarse_solve_multi(M, r1, W.et[1], nr, s);
     return;
   }
+  auto iters = [&](int i) {
+    if (i == 1) return o.n_f;
+    return (o.skip_square_levels && square_level(M, i)) ? 0 : o.n_c;
+  };
   const double* ri = r1;
   for (int i = 1; i < l; ++i) {
-    const int ni = (i == 1) ? o.n_f : o.n_c;
+    const int ni = iters(i);
     const int64_t N = level_size(M, i);
     smooth_multi(M, i, f32, ri, nullptr, ni, W.et[i], W.cr, nr, s);   // e~_i = Iter(A_i, r_i, 0)
     if (o.explicit_restrict_residual) {                              // r_i - A_i e~_i, explicitly
@@ -387,7 +417,7 @@ static void vcycle_core(Matrix& M, const h2mg_solve_opts& o, const double* r1, i
   }
   coarse_solve_multi(M, W.r[l], W.et[l], nr, s);                     // e_l = dir_sol(A_l, r_l)
   for (int i = l - 1; i >= 1; --i) {
-    const int ni = (i == 1) ? o.n_f : o.n_c;
+    const int ni = iters(i);
     prolong_add_multi(M, i, W.et[i + 1], W.et[i], nr, s);            // e~_i += V_i^T e_{i+1}
     const double* fi = (i == 1) ? r1 : W.r[i];
     smooth_multi(M, i, f32, fi, W.et[i], ni, W.et[i], nullptr, nr, s);   // e_i = Iter(A_i, r_i, e~_i)
@@ -411,11 +441,13 @@ void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double*
 
 // ----------------------------------------------------------------------------- graphs
 // A V-cycle (vcycle_core on the solve's residual buffer) captured once per solve
-// setting and column count, then replayed with one launch per outer iteration.
+// setting and column count; replayed with one launch per outer iteration, or used as
+// one branch of a graph over several independent problems.
 struct GraphEntry {
-  int nr, n_f, n_c, f32, err;
-  cudaGraphExec_t exec = nullptr;
-  int64_t launches = 0;   // kernels per replay
+  int nr, n_f, n_c, f32, err, skip;
+  cudaGraph_t graph = nullptr;        // the captured sequence
+  cudaGraphExec_t exec = nullptr;     // instantiated on first replay
+  int64_t launches = 0;               // kernels per replay
 };
 struct GraphSet {
   std::vector<GraphEntry> g;
@@ -423,8 +455,10 @@ struct GraphSet {
 
 void destroy_graphs(Matrix& M) {
   if (M.graphs) {
-    for (auto& e : M.graphs->g)
+    for (auto& e : M.graphs->g) {
       if (e.exec) best_effort(cudaGraphExecDestroy(e.exec), "cudaGraphExecDestroy");
+      if (e.graph) best_effort(cudaGraphDestroy(e.graph), "cudaGraphDestroy");
+    }
     delete M.graphs;
     M.graphs = nullptr;
   }
@@ -434,32 +468,30 @@ void destroy_graphs(Matrix& M) {
   }
 }
 
-static const GraphEntry& vcycle_graph(Matrix& M, const h2mg_solve_opts& o, int nr) {
+static GraphEntry& vcycle_graph(Matrix& M, const h2mg_solve_opts& o, int nr) {
   if (!M.graphs) M.graphs = new GraphSet();
   const int f32 = o.precision == H2MG_PREC_MIXED_F32;
-  for (const GraphEntry& e : M.graphs->g)
-    if (e.nr == nr && e.n_f == o.n_f && e.n_c == o.n_c && e.f32 == f32 && e.err == o.explicit_restrict_residual)
+  for (GraphEntry& e : M.graphs->g)
+    if (e.nr == nr && e.n_f == o.n_f && e.n_c == o.n_c && e.f32 == f32 && e.err == o.explicit_restrict_residual &&
+        e.skip == o.skip_square_levels)
       return e;
   if (!M.cap_stream) H2_CUDA(cudaStreamCreateWithFlags(&M.cap_stream, cudaStreamNonBlocking));
   Work W = work(M);
-  GraphEntry e{nr, o.n_f, o.n_c, f32, o.explicit_restrict_residual};
-  cudaGraph_t graph = nullptr;
+  GraphEntry e{nr, o.n_f, o.n_c, f32, o.explicit_restrict_residual, o.skip_square_levels};
   const int64_t l0 = h2mg_launch_count();
   H2_CUDA(cudaStreamBeginCapture(M.cap_stream, cudaStreamCaptureModeThreadLocal));
   try {
     vcycle_core(M, o, W.t1, nr, M.cap_stream);
   } catch (...) {
-    best_effort(cudaStreamEndCapture(M.cap_stream, &graph), "cudaStreamEndCapture (after an error)");
-    if (graph) best_effort(cudaGraphDestroy(graph), "cudaGraphDestroy (after an error)");
+    cudaGraph_t g = nullptr;
+    best_effort(cudaStreamEndCapture(M.cap_stream, &g), "cudaStreamEndCapture (after an error)");
+    if (g) best_effort(cudaGraphDestroy(g), "cudaGraphDestroy (after an error)");
     add_launches(l0 - h2mg_launch_count());
     throw;
   }
   e.launches = h2mg_launch_count() - l0;
   add_launches(-e.launches);   // captured, not run
-  H2_CUDA(cudaStreamEndCapture(M.cap_stream, &graph));
-  const cudaError_t err = cudaGraphInstantiate(&e.exec, graph, 0);
-  best_effort(cudaGraphDestroy(graph), "cudaGraphDestroy");
-  H2_CUDA(err);
+  H2_CUDA(cudaStreamEndCapture(M.cap_stream, &e.graph));
   M.graphs->g.push_back(e);
   return M.graphs->g.back();
 }
@@ -473,7 +505,8 @@ static void vcycle_solve_step(Matrix& M, const h2mg_solve_opts& o, int nr, cudaS
     vcycle_core(M, o, W.t1, nr, s);
     return;
   }
-  const GraphEntry& e = vcycle_graph(M, o, nr);
+  GraphEntry& e = vcycle_graph(M, o, nr);
+  if (!e.exec) H2_CUDA(cudaGraphInstantiate(&e.exec, e.graph, 0));
   H2_CUDA(cudaGraphLaunch(e.exec, s));
   add_launches(e.launches);
 }
@@ -604,6 +637,205 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
   for (int c = 0; c < nr; ++c) {
     info[c].ms_solve = ms;
     if (!info[c].converged) st = H2MG_ERR_NOT_CONVERGED;
+  }
+  if (nan) st = H2MG_ERR_NAN;
+  return st;
+}
+
+// ----------------------------------------------------------------------------- many problems
+// Pinned host copies of dot-product partials of several problems, read with one
+// synchronisation.
+struct HostParts {
+  double* h = nullptr;
+  explicit HostParts(size_t n) { H2_CUDA(cudaMallocHost(&h, sizeof(double) * n)); }
+  ~HostParts() {
+    if (h) best_effort(cudaFreeHost(h), "cudaFreeHost");
+  }
+};
+
+// out[p] = a_p^T b_p for every problem p with want[p], one synchronisation in all.
+static void dots_many(const std::vector<Matrix*>& Ms, const std::vector<const double*>& a,
+                      const std::vector<const double*>& b, const std::vector<char>& want, HostParts& hp,
+                      double* out, cudaStream_t s) {
+  const size_t P = Ms.size();
+  for (size_t p = 0; p < P; ++p) {
+    if (!want[p]) continue;
+    Work W = work(*Ms[p]);
+    dot_part(a[p], b[p], Ms[p]->n, Ms[p]->n, 1, W.pa, s);
+    H2_CUDA(cudaMemcpyAsync(hp.h + p * NPART, W.pa, sizeof(double) * part_grid(Ms[p]->n), cudaMemcpyDeviceToHost,
+                            s));
+  }
+  H2_CUDA(cudaStreamSynchronize(s));
+  for (size_t p = 0; p < P; ++p) {
+    if (!want[p]) continue;
+    double t = 0.0;
+    for (int i = 0; i < part_grid(Ms[p]->n); ++i) t += hp.h[p * NPART + i];
+    out[p] = t;
+  }
+}
+
+// One graph whose branches are the captured V-cycles of the problems in `sel`:
+// independent branches, so the kernels of different problems run concurrently.
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+  std::vector<char> sel;
+  ~BatchGraph() {
+    if (exec) best_effort(cudaGraphExecDestroy(exec), "cudaGraphExecDestroy (batch)");
+  }
+  void build(const std::vector<Matrix*>& Ms, const h2mg_solve_opts& o, const std::vector<char>& active) {
+    if (exec) {
+      best_effort(cudaGraphExecDestroy(exec), "cudaGraphExecDestroy (batch)");
+      exec = nullptr;
+    }
+    cudaGraph_t G = nullptr;
+    H2_CUDA(cudaGraphCreate(&G, 0));
+    launches = 0;
+    try {
+      for (size_t p = 0; p < Ms.size(); ++p) {
+        if (!active[p]) continue;
+        GraphEntry& e = vcycle_graph(*Ms[p], o, 1);
+        cudaGraphNode_t node;
+        H2_CUDA(cudaGraphAddChildGraphNode(&node, G, nullptr, 0, e.graph));
+        launches += e.launches;
+      }
+      H2_CUDA(cudaGraphInstantiate(&exec, G, 0));
+    } catch (...) {
+      best_effort(cudaGraphDestroy(G), "cudaGraphDestroy (batch)");
+      throw;
+    }
+    best_effort(cudaGraphDestroy(G), "cudaGraphDestroy (batch)");
+    sel = active;
+  }
+};
+
+// Independent problems A_p x_p = b_p (one column each) solved together by the outer
+// iteration of solve_multi: every outer iteration computes all residuals (one
+// synchronisation for all norms), runs the V-cycles of all unconverged problems
+// (with use_graph: one launch of a graph with one branch per problem, rebuilt when
+// half of its problems have converged; a converged problem's branch then runs on its
+// last residual and is ignored), and the outer updates (one synchronisation per group
+// of dot products).
+h2mg_status solve_batched(const std::vector<Matrix*>& Ms, const double* const* b, double* const* x,
+                          const h2mg_solve_opts& o, h2mg_solve_info* info, cudaStream_t s) {
+  const size_t P = Ms.size();
+  auto t0 = std::chrono::steady_clock::now();
+  HostParts hp(P * NPART);
+  std::vector<char> all(P, 1), done(P, 0), act(P, 1);
+  std::vector<double> nb(P), rel(P), d1(P), d2(P);
+  std::vector<const double*> va(P), vb(P);
+  std::vector<double *> r(P), pv(P), q(P), pp(P), qp(P), t2(P);
+  for (size_t p = 0; p < P; ++p) {
+    Work W = work(*Ms[p]);
+    r[p] = W.t1;
+    t2[p] = W.t2;
+    const int64_t n = Ms[p]->n;
+    pv[p] = (double*)Ms[p]->wfcg.p;
+    q[p] = pv[p] + n * NRMAX;
+    pp[p] = q[p] + n * NRMAX;
+    qp[p] = pp[p] + n * NRMAX;
+    va[p] = b[p];
+    vb[p] = b[p];
+    info[p] = h2mg_solve_info{};
+  }
+  dots_many(Ms, va, vb, all, hp, nb.data(), s);
+  for (size_t p = 0; p < P; ++p) {
+    H2_REQUIRE(std::isfinite(nb[p]), H2MG_ERR_NAN, "right-hand side is not finite");
+    nb[p] = std::sqrt(nb[p]);
+  }
+  const bool fcg = o.outer == H2MG_OUTER_FCG;
+  BatchGraph bg;
+  bool nan = false;
+  for (int cyc = 0; cyc <= o.max_cycles; ++cyc) {
+    for (size_t p = 0; p < P; ++p) {
+      act[p] = !done[p];
+      if (!act[p]) continue;
+      const int64_t n = Ms[p]->n;
+      apply_level_multi(*Ms[p], 1, false, x[p], n, t2[p], n, 1, s);
+      { k_sub<<<vec_grid(n), 256, 0, s>>>(b[p], t2[p], r[p], n); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+      va[p] = r[p];
+      vb[p] = r[p];
+    }
+    dots_many(Ms, va, vb, act, hp, rel.data(), s);
+    size_t left = 0;
+    for (size_t p = 0; p < P; ++p) {
+      if (!act[p]) continue;
+      const double rr = nb[p] > 0 ? std::sqrt(rel[p]) / nb[p] : 0.0;
+      if (cyc < 256) info[p].relres_hist[cyc] = rr;
+      info[p].cycles = cyc;
+      info[p].relres = rr;
+      if (!std::isfinite(rr)) {
+        nan = true;
+        done[p] = 1;
+      } else if (rr <= o.tol) {
+        info[p].converged = 1;
+        done[p] = 1;
+      }
+      left += !done[p];
+    }
+    if (left == 0 || nan || cyc == o.max_cycles) break;
+    for (size_t p = 0; p < P; ++p) act[p] = !done[p];
+    // V-cycles of every unconverged problem: W.et[1] = V(r)
+    if (o.use_graph && !Ms[0]->prof.on) {
+      size_t built = 0;
+      for (char c : bg.sel) built += c;
+      if (!bg.exec || left * 2 <= built) bg.build(Ms, o, act);
+      H2_CUDA(cudaGraphLaunch(bg.exec, s));
+      add_launches(bg.launches);
+    } else {
+      for (size_t p = 0; p < P; ++p)
+        if (act[p]) vcycle_core(*Ms[p], o, r[p], 1, s);
+    }
+    std::vector<double> alpha(P, 0.0);
+    if (!fcg) {
+      for (size_t p = 0; p < P; ++p)
+        if (act[p]) {
+          const double one = 1.0;
+          axpy_cols(*Ms[p], &one, work(*Ms[p]).et[1], x[p], Ms[p]->n, 1, s);   // x* = x0 + e_1
+        }
+      continue;
+    }
+    for (size_t p = 0; p < P; ++p)
+      if (act[p])
+        H2_CUDA(cudaMemcpyAsync(pv[p], work(*Ms[p]).et[1], sizeof(double) * Ms[p]->n, cudaMemcpyDeviceToDevice, s));
+    if (cyc > 0) {
+      for (size_t p = 0; p < P; ++p) {
+        va[p] = work(*Ms[p]).et[1];
+        vb[p] = qp[p];
+      }
+      dots_many(Ms, va, vb, act, hp, d1.data(), s);
+      for (size_t p = 0; p < P; ++p) va[p] = pp[p];
+      dots_many(Ms, va, vb, act, hp, d2.data(), s);
+      for (size_t p = 0; p < P; ++p)
+        if (act[p]) {
+          const double beta = d2[p] != 0.0 ? -d1[p] / d2[p] : 0.0;
+          axpy_cols(*Ms[p], &beta, pp[p], pv[p], Ms[p]->n, 1, s);   // p = z + beta p_prev
+        }
+    }
+    for (size_t p = 0; p < P; ++p)
+      if (act[p]) apply_level_multi(*Ms[p], 1, false, pv[p], Ms[p]->n, q[p], Ms[p]->n, 1, s);
+    for (size_t p = 0; p < P; ++p) {
+      va[p] = pv[p];
+      vb[p] = r[p];
+    }
+    dots_many(Ms, va, vb, act, hp, d1.data(), s);
+    for (size_t p = 0; p < P; ++p) vb[p] = q[p];
+    dots_many(Ms, va, vb, act, hp, d2.data(), s);
+    for (size_t p = 0; p < P; ++p)
+      if (act[p]) {
+        const double al = d2[p] > 0.0 ? d1[p] / d2[p] : 0.0;
+        axpy_cols(*Ms[p], &al, pv[p], x[p], Ms[p]->n, 1, s);        // x += alpha p
+        std::swap(pv[p], pp[p]);
+        std::swap(q[p], qp[p]);
+      }
+  }
+  H2_CUDA(cudaStreamSynchronize(s));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h2mg_status st = H2MG_OK;
+  for (size_t p = 0; p < P; ++p) {
+    info[p].ms_solve = ms;
+    if (!info[p].converged) st = H2MG_ERR_NOT_CONVERGED;
   }
   if (nan) st = H2MG_ERR_NAN;
   return st;

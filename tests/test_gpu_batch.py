@@ -170,3 +170,68 @@ def test_graph_replayed_vcycle_matches_direct_launches(w1, nrhs):
     assert l1 - l0 > 0 and l2 - l1 > 0
     # every V-cycle runs at least one block product per level and smoother step
     assert nk >= max(i.cycles for i in ig2) and kms > 0 and kby > 0
+
+
+@pytest.fixture(scope="module")
+def uneven():
+    """Independent problems of uneven size and kind: three perturbed spheres with the
+    single-layer kernel (sizes from the surface workload's list) and the 4096-point
+    exponential point cloud."""
+    from oracle import surface_diag
+    ms = sorted(set(W.surface_problem_sizes()))[:3]
+    probs = []
+    for j, m in enumerate(ms):
+        c, a, _ = W.perturbed_icosphere(m, j)
+        A = pkg.H2Matrix(torch.from_numpy(c).cuda(), "laplace_sl", weights=torch.from_numpy(a).cuda(), leaf=64, q=4,
+                         with_f32=True)
+        h = H2Matrix(c, KernelSpec("laplace_sl", 1.0, 0.0, 2, a, surface_diag(a)), 64, 4, 1.0)
+        probs.append((A, h, W.normal_rhs(c.shape[0], 3 + j)))
+    p = W.workload(1)
+    A = pkg.H2Matrix(torch.from_numpy(p["points"]).cuda(), "exponential", length=0.1, nugget=1e-2, leaf=64, q=4,
+                     with_f32=True)
+    h = H2Matrix(p["points"], KernelSpec("exponential", 0.1, 1e-2), 64, 4, 1.0)
+    probs.append((A, h, p["b"]))
+    yield probs
+    for A, _, _ in probs:
+        A.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_independent_problems_solved_together_like_oracle(uneven, use_graph):
+    tol = 1e-9
+    mats = [A for A, _, _ in uneven]
+    bs = [torch.from_numpy(b).cuda() for _, _, b in uneven]
+    xs, infos = pkg.solve_batched(mats, bs, tol=tol, max_cycles=300, outer="fcg", use_graph=use_graph)
+    assert len(infos) == len(uneven)
+    for (A, h, b), x, info in zip(uneven, xs, infos):
+        assert info.converged
+        r = b - h.apply(x.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= tol * 1.0001
+        _, io = solve_fcg(H2MG(h), b, SolveOpts(tol=tol, max_cycles=300))
+        assert abs(info.cycles - io.cycles) <= max(2, 0.15 * io.cycles), (info.cycles, io.cycles)
+        # the same problem alone on the GPU
+        _, i1 = A.solve(torch.from_numpy(b).cuda(), tol=tol, max_cycles=300, outer="fcg")
+        assert abs(info.cycles - i1.cycles) <= max(2, 0.15 * i1.cycles)
+
+
+def test_independent_problems_mixed_precision_host_buffers(uneven):
+    mats = [A for A, _, _ in uneven]
+    bs = [b.copy() for _, _, b in uneven]
+    xs, infos = pkg.solve_batched(mats, bs, tol=1e-10, max_cycles=300, outer="fcg", precision="mixed_f32",
+                                  use_graph=True)
+    for (A, h, b), x, info in zip(uneven, xs, infos):
+        assert isinstance(x, np.ndarray) and info.converged
+        assert np.linalg.norm(b - h.apply(x)) / np.linalg.norm(b) <= 1e-10 * 1.0001
+
+
+def test_independent_problems_reject_duplicates_and_report_per_problem(uneven):
+    A0 = uneven[0][0]
+    b0 = torch.from_numpy(uneven[0][2]).cuda()
+    with pytest.raises(pkg.H2MGError) as e:
+        pkg.solve_batched([A0, A0], [b0, b0.clone()])
+    assert e.value.name == "INVALID_ARG"
+    # a problem that cannot converge in one cycle is reported per problem
+    mats = [A for A, _, _ in uneven]
+    bs = [torch.from_numpy(b).cuda() for _, _, b in uneven]
+    xs, infos = pkg.solve_batched(mats, bs, tol=1e-17, max_cycles=1, raise_on_fail=False, outer="fcg")
+    assert all(i.cycles == 1 and not i.converged for i in infos)

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import H2MG, H2Matrix, KernelSpec, SolveOpts, dense_kernel_matrix, solve, surface_diag
+from oracle import H2MG, H2Matrix, KernelSpec, SolveOpts, dense_kernel_matrix, solve, solve_fcg, surface_diag
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -191,6 +191,14 @@ def test_vcycle_matches_oracle_short_smoothing(pair):
     xg = A.vcycle(cuda(x0), cuda(b), n_f=1, n_c=2).cpu().numpy()
     xo = vcycle(mg, x0, b, o)
     assert rel(xg, xo) < 1e-9, name
+    # no smoothing where the restriction is square (the GPU decides per cluster, the
+    # oracle by level sizes)
+    o2 = SolveOpts(n_f=1, n_c=2, skip_square_levels=True)
+    xg2 = A.vcycle(cuda(x0), cuda(b), n_f=1, n_c=2, skip_square_levels=True).cpu().numpy()
+    xo2 = vcycle(mg, x0, b, o2)
+    assert rel(xg2, xo2) < 1e-9, name
+    square = any(mg.size(i) == mg.size(i - 1) for i in range(2, mg.l))
+    assert (rel(xo2, xo) > 1e-6) == square, name
 
 
 def test_solve_cycles_match_oracle():
@@ -241,11 +249,52 @@ def test_polynomial_kernel_full_size_rows():
 
 
 def test_surface_kernel_weights_and_diagonal():
+    """Single-layer kernel on a perturbed sphere: the library forms the panel
+    self-interaction from the areas itself; the oracle from its own formula."""
     c, a, _ = W.perturbed_icosphere(12, 0)
-    dg = surface_diag(a)
-    A, h = build_pair(c, "laplace_sl", 1.0, 0.0, 64, 3, weights=a, diag=dg)
+    A = pkg.H2Matrix(cuda(c), "laplace_sl", weights=cuda(a), leaf=64, q=3)
+    h = H2Matrix(c, KernelSpec("laplace_sl", 1.0, 0.0, 2, a, surface_diag(a)), 64, 3, 1.0)
     x = np.random.default_rng(8).standard_normal(c.shape[0])
     assert rel(A.apply(cuda(x)).cpu().numpy(), h.apply(x)) < 1e-12
+    # an explicit diagonal override is used as given
+    dg = np.random.default_rng(9).uniform(0.01, 0.02, c.shape[0])
+    A2, h2 = build_pair(c, "laplace_sl", 1.0, 0.0, 64, 3, weights=a, diag=dg)
+    assert rel(A2.apply(cuda(x)).cpu().numpy(), h2.apply(x)) < 1e-12
+    A.close()
+    A2.close()
+
+
+def test_fp32_product_after_float64_product_on_ragged_leaves():
+    """Leaves of about 40 points padded to 64 slots: the FP32 product must not read
+    what a float64 product left in the shared point buffer (as floats those bytes can
+    be NaN)."""
+    c, a, _ = W.perturbed_icosphere(16, 0)
+    A = pkg.H2Matrix(cuda(c), "laplace_sl", weights=cuda(a), leaf=64, q=4, with_f32=True)
+    x = cuda(np.random.default_rng(2).standard_normal(c.shape[0]))
+    for _ in range(2):
+        y64 = A.apply_level(1, x, "f64")
+        y32 = A.apply_level(1, x, "mixed_f32")
+        assert bool(torch.isfinite(y32).all())
+        assert float((y32 - y64).norm() / y64.norm()) < 1e-5
+        X = torch.stack([x, 2 * x, -x, x]).t()
+        A.apply(X)                                   # two-column float64 groups
+    A.close()
+
+
+@pytest.mark.parametrize("m,j", [(20, 1), (16, 0)])
+def test_surface_problem_solves_like_oracle(m, j):
+    c, a, _ = W.perturbed_icosphere(m, j)
+    A = pkg.H2Matrix(cuda(c), "laplace_sl", weights=cuda(a), leaf=64, q=4, with_f32=True)
+    h = H2Matrix(c, KernelSpec("laplace_sl", 1.0, 0.0, 2, a, surface_diag(a)), 64, 4, 1.0)
+    b = W.normal_rhs(c.shape[0], 3)
+    _, io = solve_fcg(H2MG(h), b, SolveOpts(tol=1e-10, max_cycles=50))
+    for prec in ("f64", "mixed_f32"):
+        x, info = A.solve(cuda(b), tol=1e-10, max_cycles=50, outer="fcg", precision=prec)
+        assert info.converged and io.converged
+        assert abs(info.cycles - io.cycles) <= 2, (prec, info.cycles, io.cycles)
+        r = b - h.apply(x.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10 * 1.0001
+    A.close()
 
 
 def test_mixed_precision_solve_reaches_float64_tolerance():

@@ -343,3 +343,65 @@ def test_icosphere_geometry():
     r = np.linalg.norm(v, axis=2)
     assert r.min() >= 0.8 - 1e-12 and r.max() <= 1.2 + 1e-12
     assert abs(abs(r - 1).max() - 0.2) < 1e-12
+
+
+def test_surface_self_interaction_is_the_disk_potential():
+    """The single-layer diagonal (Sec. 4.3, symmetric scaling) is the potential at the
+    centre of a flat unit-density disk of the panel's area, checked by adaptive
+    Cartesian quadrature of 1 / (4 pi |y|) over the quarter disk (times four)."""
+    from scipy.integrate import dblquad
+
+    from oracle import surface_diag
+    for area in (1e-3, 0.05, 2.0):
+        R = math.sqrt(area / math.pi)
+        q, _ = dblquad(lambda y, x: 1.0 / (4 * math.pi * math.hypot(x, y)), 0.0, R,
+                       0.0, lambda x: math.sqrt(max(R * R - x * x, 0.0)), epsabs=1e-14, epsrel=1e-10)
+        val = 4 * q
+        assert abs(surface_diag(np.array([area]))[0] - val) <= 1e-7 * val, (area, val)
+    # scaling: a length, like the off-diagonal sqrt(a a) / (4 pi r)
+    assert math.isclose(surface_diag(np.array([4.0]))[0], 2 * surface_diag(np.array([1.0]))[0])
+
+
+def test_surface_matrix_is_positive_definite():
+    """With the disk self-interaction the dense single-layer matrix of a perturbed
+    sphere is positive definite (and reasonably conditioned); the formula with an extra
+    factor of the area on the diagonal is not."""
+    from oracle import surface_diag
+    c, a, _ = W.perturbed_icosphere(8, 1)
+    A = dense_kernel_matrix("laplace_sl", c, 1.0, 0.0, weights=a, diag=surface_diag(a))
+    ev = np.linalg.eigvalsh(A)
+    assert ev[0] > 0 and ev[-1] / ev[0] < 1e3
+    B = A.copy()
+    np.fill_diagonal(B, a * np.sqrt(a / math.pi) / 2)
+    assert np.linalg.eigvalsh(B)[0] < 0
+
+
+def test_skip_square_levels():
+    """Option skip_square_levels: a level whose restriction is square (as many basis
+    columns as rows in every cluster) gets no smoothing. Where no level is square it
+    changes nothing; where one is, the cycle still contracts the energy norm of the
+    error and the solve still reaches the dense solution."""
+    from oracle.mg import vcycle
+    # 2-D, 4 x 4 nodes < 64 points per leaf: no square level
+    X2 = W.uniform_points(2048, 2, 3)
+    mg2 = H2MG(H2Matrix(X2, KernelSpec("exponential", 0.1, 1e-2), 64, 4, 1.0))
+    assert all(mg2.size(i) < mg2.size(i - 1) for i in range(2, mg2.l + 1))
+    r = np.random.default_rng(5).standard_normal(2048)
+    a = vcycle(mg2, np.zeros(2048), r, SolveOpts(n_f=1, n_c=5))
+    b = vcycle(mg2, np.zeros(2048), r, SolveOpts(n_f=1, n_c=5, skip_square_levels=True))
+    assert np.array_equal(a, b)
+    # 3-D, 2 x 2 x 2 nodes and leaves of 8 points: U_1 is square
+    X3 = W.uniform_points(1024, 3, 3)
+    h3 = H2Matrix(X3, KernelSpec("gaussian", 0.2, 1e-1), 8, 2, 1.0)
+    mg3 = H2MG(h3)
+    assert mg3.size(2) == mg3.size(1)
+    o = SolveOpts(tol=1e-10, max_cycles=200, n_f=1, n_c=10, skip_square_levels=True)
+    Ad = h3.dense()
+    xt = np.random.default_rng(6).standard_normal(1024)
+    bb = Ad @ xt
+    x1 = vcycle(mg3, np.zeros(1024), bb, o)
+    e0, e1 = xt, xt - x1
+    assert e1 @ Ad @ e1 < e0 @ Ad @ e0
+    x, info = solve(mg3, bb, o)
+    assert info.converged
+    assert np.linalg.norm(x - np.linalg.solve(Ad, bb)) <= np.linalg.cond(Ad) * 1e-10 * np.linalg.norm(xt)
