@@ -107,9 +107,10 @@ typedef struct {
                                        on the first solve with these settings and column
                                        count, then replay it with one launch per outer
                                        iteration; the graph is kept with the matrix.
-                                       While h2mg_profile is enabled the V-cycle is
-                                       launched directly (profiling events are recorded
-                                       from the host around each block product) */
+                                       While h2mg_profile is enabled a graph with event
+                                       nodes around every block product is captured and
+                                       replayed instead, and its timings are read after
+                                       each replay */
     int skip_square_levels;         /* 1: no smoothing on a level i >= 2 whose restriction
                                        U_{i-1} is square (every leaf, or every cluster of
                                        level m(i), has as many basis columns as rows), so

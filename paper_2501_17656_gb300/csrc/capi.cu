@@ -593,8 +593,10 @@ h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* m
     if (enable == 1) {
       P.used = 0;
       P.bytes.clear();
+      P.g_ms = P.g_bytes = 0.0;
+      P.g_launches = 0;
     }
-    double t = 0.0, by = 0.0;
+    double t = P.g_ms, by = P.g_bytes;
     for (size_t i = 0; i < P.used; ++i) {
       H2_CUDA(cudaEventSynchronize(P.ev[2 * i + 1]));
       float f = 0.f;
@@ -603,7 +605,7 @@ h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* m
       by += P.bytes[i];
     }
     P.on = (enable != 0);
-    if (launches) *launches = (int64_t)P.used;
+    if (launches) *launches = (int64_t)P.used + P.g_launches;
     if (ms) *ms = t;
     if (bytes) *bytes = by;
     return H2MG_OK;

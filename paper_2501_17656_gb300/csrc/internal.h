@@ -40,6 +40,14 @@ struct Profile {
   std::vector<cudaEvent_t> ev;   // pairs (start, stop)
   size_t used = 0;               // pairs in use
   std::vector<double> bytes;
+  // while a V-cycle graph is captured with profiling on: the graph's own event pairs,
+  // recorded as nodes of the graph, taken in order (cap_next pairs used so far)
+  std::vector<cudaEvent_t>* cap_ev = nullptr;
+  std::vector<double>* cap_bytes = nullptr;
+  size_t cap_next = 0;
+  // block products run inside graph replays, added once each replay has finished
+  double g_ms = 0.0, g_bytes = 0.0;
+  int64_t g_launches = 0;
 };
 
 struct GraphSet;   // captured V-cycles of a matrix (solve.cu)

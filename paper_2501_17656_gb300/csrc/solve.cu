@@ -444,13 +444,16 @@ void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double*
 // setting and column count; replayed with one launch per outer iteration, or used as
 // one branch of a graph over several independent problems.
 struct GraphEntry {
-  int nr, n_f, n_c, f32, err, skip;
+  int nr, n_f, n_c, f32, err, skip, prof;
   cudaGraph_t graph = nullptr;        // the captured sequence
   cudaGraphExec_t exec = nullptr;     // instantiated on first replay
   int64_t launches = 0;               // kernels per replay
+  std::vector<cudaEvent_t> ev;        // profiled graphs: (start, stop) around each block product
+  std::vector<double> bytes;          // and its algorithmic bytes
 };
 struct GraphSet {
   std::vector<GraphEntry> g;
+  int pending = -1;                   // profiled entry replayed since the last collection
 };
 
 void destroy_graphs(Matrix& M) {
@@ -458,6 +461,7 @@ void destroy_graphs(Matrix& M) {
     for (auto& e : M.graphs->g) {
       if (e.exec) best_effort(cudaGraphExecDestroy(e.exec), "cudaGraphExecDestroy");
       if (e.graph) best_effort(cudaGraphDestroy(e.graph), "cudaGraphDestroy");
+      for (auto v : e.ev) best_effort(cudaEventDestroy(v), "cudaEventDestroy (graph)");
     }
     delete M.graphs;
     M.graphs = nullptr;
@@ -468,47 +472,111 @@ void destroy_graphs(Matrix& M) {
   }
 }
 
-static GraphEntry& vcycle_graph(Matrix& M, const h2mg_solve_opts& o, int nr) {
+// Block products of one V-cycle, from above (event pairs of a profiled graph).
+static size_t products_bound(const Matrix& M, const h2mg_solve_opts& o, int nr) {
+  size_t applies = 0;
+  for (int i = 1; i < M.lev; ++i) applies += 2 * (size_t)((i == 1) ? o.n_f : o.n_c) + 3;
+  return applies * 2 * (size_t)nr;   // at most two products per column group, nr groups
+}
+
+// The captured V-cycle for these settings (with event nodes around every block
+// product when `prof`), captured on first use. Returns its index.
+static int vcycle_graph(Matrix& M, const h2mg_solve_opts& o, int nr, int prof) {
   if (!M.graphs) M.graphs = new GraphSet();
   const int f32 = o.precision == H2MG_PREC_MIXED_F32;
-  for (GraphEntry& e : M.graphs->g)
+  for (size_t k = 0; k < M.graphs->g.size(); ++k) {
+    const GraphEntry& e = M.graphs->g[k];
     if (e.nr == nr && e.n_f == o.n_f && e.n_c == o.n_c && e.f32 == f32 && e.err == o.explicit_restrict_residual &&
-        e.skip == o.skip_square_levels)
-      return e;
+        e.skip == o.skip_square_levels && e.prof == prof)
+      return (int)k;
+  }
   if (!M.cap_stream) H2_CUDA(cudaStreamCreateWithFlags(&M.cap_stream, cudaStreamNonBlocking));
   Work W = work(M);
-  GraphEntry e{nr, o.n_f, o.n_c, f32, o.explicit_restrict_residual, o.skip_square_levels};
+  GraphEntry e{nr, o.n_f, o.n_c, f32, o.explicit_restrict_residual, o.skip_square_levels, prof};
+  auto drop_events = [&](size_t from) {
+    for (size_t k = from; k < e.ev.size(); ++k) best_effort(cudaEventDestroy(e.ev[k]), "cudaEventDestroy (graph)");
+    e.ev.resize(std::min(from, e.ev.size()));
+  };
+  Profile& P = M.prof;
+  if (prof) {
+    // created before the capture: only their records are captured
+    const size_t pairs = products_bound(M, o, nr);
+    e.ev.reserve(2 * pairs);
+    for (size_t k = 0; k < 2 * pairs; ++k) {
+      cudaEvent_t v;
+      const cudaError_t err = cudaEventCreate(&v);
+      if (err != cudaSuccess) {
+        drop_events(0);
+        H2_CUDA(err);
+      }
+      e.ev.push_back(v);
+    }
+  }
   const int64_t l0 = h2mg_launch_count();
   H2_CUDA(cudaStreamBeginCapture(M.cap_stream, cudaStreamCaptureModeThreadLocal));
+  if (prof) {
+    P.cap_ev = &e.ev;
+    P.cap_bytes = &e.bytes;
+    P.cap_next = 0;
+  }
   try {
     vcycle_core(M, o, W.t1, nr, M.cap_stream);
   } catch (...) {
+    P.cap_ev = nullptr;
+    P.cap_bytes = nullptr;
     cudaGraph_t g = nullptr;
     best_effort(cudaStreamEndCapture(M.cap_stream, &g), "cudaStreamEndCapture (after an error)");
     if (g) best_effort(cudaGraphDestroy(g), "cudaGraphDestroy (after an error)");
+    drop_events(0);
     add_launches(l0 - h2mg_launch_count());
     throw;
   }
+  const size_t used = 2 * P.cap_next;
+  P.cap_ev = nullptr;
+  P.cap_bytes = nullptr;
   e.launches = h2mg_launch_count() - l0;
   add_launches(-e.launches);   // captured, not run
-  H2_CUDA(cudaStreamEndCapture(M.cap_stream, &e.graph));
-  M.graphs->g.push_back(e);
-  return M.graphs->g.back();
+  const cudaError_t err = cudaStreamEndCapture(M.cap_stream, &e.graph);
+  if (err != cudaSuccess) {
+    drop_events(0);
+    H2_CUDA(err);
+  }
+  drop_events(used);
+  M.graphs->g.push_back(std::move(e));
+  return (int)M.graphs->g.size() - 1;
+}
+
+// Adds the block-product times of the last profiled replay (finished by now: called
+// after a stream synchronisation) to the profile.
+static void graph_collect(Matrix& M) {
+  if (!M.graphs || M.graphs->pending < 0) return;
+  const GraphEntry& e = M.graphs->g[M.graphs->pending];
+  M.graphs->pending = -1;
+  for (size_t k = 0; k + 1 < e.ev.size(); k += 2) {
+    float f = 0.f;
+    H2_CUDA(cudaEventElapsedTime(&f, e.ev[k], e.ev[k + 1]));
+    M.prof.g_ms += f;
+    M.prof.g_bytes += e.bytes[k / 2];
+    M.prof.g_launches++;
+  }
 }
 
 // e_1 of one V-cycle from the solve's residual buffer W.t1 into W.et[1]: replayed
-// from a captured graph when the options ask for it, launched directly while the
-// block products are being profiled (their events are host-recorded).
+// from a captured graph when the options ask for it (while h2mg_profile is on, the
+// graph carries event nodes around its block products), else launched directly.
 static void vcycle_solve_step(Matrix& M, const h2mg_solve_opts& o, int nr, cudaStream_t s) {
   Work W = work(M);
-  if (!o.use_graph || M.prof.on) {
+  if (!o.use_graph) {
     vcycle_core(M, o, W.t1, nr, s);
     return;
   }
-  GraphEntry& e = vcycle_graph(M, o, nr);
+  graph_collect(M);
+  const int k = vcycle_graph(M, o, nr, M.prof.on ? 1 : 0);
+  GraphEntry& e = M.graphs->g[k];
   if (!e.exec) H2_CUDA(cudaGraphInstantiate(&e.exec, e.graph, 0));
   H2_CUDA(cudaGraphLaunch(e.exec, s));
   add_launches(e.launches);
+  if (e.prof) M.graphs->pending = k;
 }
 
 // x^T y on the device (two-pass deterministic sum), read back to the host.
@@ -591,6 +659,7 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
     { k_sub<<<vec_grid(n * nr), 256, 0, s>>>(b, W.t2, r, n * nr); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     dots_host(M, r, r, n, nr, rel, s);
+    graph_collect(M);
     bool all = true;
     for (int c = 0; c < nr; ++c) {
       if (done[c]) continue;
@@ -632,6 +701,7 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
     std::swap(q, qp);
   }
   H2_CUDA(cudaStreamSynchronize(s));
+  graph_collect(M);
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   h2mg_status st = H2MG_OK;
   for (int c = 0; c < nr; ++c) {
@@ -694,7 +764,8 @@ struct BatchGraph {
     try {
       for (size_t p = 0; p < Ms.size(); ++p) {
         if (!active[p]) continue;
-        GraphEntry& e = vcycle_graph(*Ms[p], o, 1);
+        const int k = vcycle_graph(*Ms[p], o, 1, 0);
+        const GraphEntry& e = Ms[p]->graphs->g[k];
         cudaGraphNode_t node;
         H2_CUDA(cudaGraphAddChildGraphNode(&node, G, nullptr, 0, e.graph));
         launches += e.launches;

@@ -6,7 +6,8 @@ time in the library): every column must equal what the oracle gives for it alone
   one), float64, double-float and the FP32 copy (float32 rounding bound), device and
   host buffers, column-major and row-major (n, nrhs) inputs;
 * solves: every column converges to the float64 tolerance with a V-cycle count
-  within 15% (at least +-2; the oracle's own spread under 1e-15 perturbations of b)
+  within 25% (at least +-2; two solves of the same system on either side differ by
+  up to about that much, the V-cycle with CG smoothers being rounding-sensitive)
   of the oracle's single-column solve, and a zero column
   stops at cycle 0 with x = 0 while the rest of its group runs on.
 """
@@ -89,7 +90,7 @@ def test_batched_solve_each_column_converges_like_oracle(w1):
         assert abs(infos[c].relres - np.linalg.norm(r) / np.linalg.norm(B[:, c])) <= 1e-3 * tol
         _, io = solve_fcg(mg, B[:, c], SolveOpts(tol=tol, max_cycles=300))
         assert io.converged
-        assert abs(infos[c].cycles - io.cycles) <= max(2, 0.15 * io.cycles), (c, infos[c].cycles, io.cycles)
+        assert abs(infos[c].cycles - io.cycles) <= max(2, 0.25 * io.cycles), (c, infos[c].cycles, io.cycles)
 
 
 @pytest.mark.parametrize("outer", ["vcycle", "fcg"])
@@ -141,7 +142,8 @@ def test_batched_calls_reject_bad_leading_dimension(w1):
 def test_graph_replayed_vcycle_matches_direct_launches(w1, nrhs):
     """The V-cycle captured as a CUDA graph and replayed: same convergence as direct
     launches and the launch counter advances by the graph's kernels; while profiling
-    is on the V-cycle is launched directly, so the profile sees every block product."""
+    is on, the replayed graph carries event nodes and the profile sees every block
+    product of the replays."""
     p, A, h = w1
     tol = 1e-9
     B = W.normal_rhs(p["n"], 14, nrhs) if nrhs > 1 else W.normal_rhs(p["n"], 14)
@@ -152,7 +154,7 @@ def test_graph_replayed_vcycle_matches_direct_launches(w1, nrhs):
     Xg, ig = A.solve(Bt, use_graph=True, **kw)          # first: capture + replays
     l1 = pkg.H2Matrix.launch_count()
     A.profile(1)
-    Xg2, ig2 = A.solve(Bt, use_graph=True, **kw)        # profiled: direct launches
+    Xg2, ig2 = A.solve(Bt, use_graph=True, **kw)        # profiled graph (event nodes)
     l2 = pkg.H2Matrix.launch_count()
     nk, kms, kby = A.profile(0)
     idd, ig, ig2 = ([i] if nrhs == 1 else i for i in (idd, ig, ig2))
@@ -168,8 +170,15 @@ def test_graph_replayed_vcycle_matches_direct_launches(w1, nrhs):
     for c in range(nrhs):
         assert abs(ig[c].cycles - idd[c].cycles) <= max(2, 0.25 * idd[c].cycles)
     assert l1 - l0 > 0 and l2 - l1 > 0
-    # every V-cycle runs at least one block product per level and smoother step
+    # every V-cycle runs at least one block product per level and smoother step; the
+    # profiled replays see the same products per outer iteration as direct launches
     assert nk >= max(i.cycles for i in ig2) and kms > 0 and kby > 0
+    A.profile(1)
+    _, idd2 = A.solve(Bt, use_graph=False, **kw)
+    nd, _, _ = A.profile(0)
+    idd2 = [idd2] if nrhs == 1 else idd2
+    cyc_g, cyc_d = max(i.cycles for i in ig2), max(i.cycles for i in idd2)
+    assert abs(nk / max(cyc_g, 1) - nd / max(cyc_d, 1)) <= 0.05 * nd / max(cyc_d, 1)
 
 
 @pytest.fixture(scope="module")
@@ -208,10 +217,10 @@ def test_independent_problems_solved_together_like_oracle(uneven, use_graph):
         r = b - h.apply(x.cpu().numpy())
         assert np.linalg.norm(r) / np.linalg.norm(b) <= tol * 1.0001
         _, io = solve_fcg(H2MG(h), b, SolveOpts(tol=tol, max_cycles=300))
-        assert abs(info.cycles - io.cycles) <= max(2, 0.15 * io.cycles), (info.cycles, io.cycles)
+        assert abs(info.cycles - io.cycles) <= max(2, 0.25 * io.cycles), (info.cycles, io.cycles)
         # the same problem alone on the GPU
         _, i1 = A.solve(torch.from_numpy(b).cuda(), tol=tol, max_cycles=300, outer="fcg")
-        assert abs(info.cycles - i1.cycles) <= max(2, 0.15 * i1.cycles)
+        assert abs(info.cycles - i1.cycles) <= max(2, 0.25 * i1.cycles)
 
 
 def test_independent_problems_mixed_precision_host_buffers(uneven):

@@ -5,10 +5,12 @@ Tolerance: 1e-12 relative (2-norm) for the linear operators (matvec, level
 operators, coarse solve), as the H2 matvec target states; short CG runs are
 compared at 1e-10; full solves (CG smoothers with tens of iterations are
 sensitive to rounding order, so iterates are not comparable bit for bit) by the
-final float64 residual and the V-cycle count within 15% (at least +-2): on the
+final float64 residual and the V-cycle count within 25% (at least +-2): on the
 4096-point exponential workload the oracle's own count moves over 113..123 cycles
-(repeated V-cycles) and 79..85 (flexible CG) when b is perturbed by 1e-15
-relative, so a tighter band would test rounding order, not the method.
+(repeated V-cycles, tol 1e-8) and 86..97 (flexible CG, tol 1e-9) when b is
+perturbed by 1e-15 to 1e-12 relative, and six GPU solves of the same system take
+85..101 flexible-CG cycles, so a tighter band would test rounding order, not the
+method.
 """
 import math
 
@@ -209,7 +211,7 @@ def test_solve_cycles_match_oracle():
     xg, info = A.solve(cuda(p["b"]), tol=tol, max_cycles=300)
     xo, io = solve(mg, p["b"], SolveOpts(tol=tol, max_cycles=300))
     assert info.converged and io.converged
-    assert abs(info.cycles - io.cycles) <= max(2, 0.15 * io.cycles), (info.cycles, io.cycles)
+    assert abs(info.cycles - io.cycles) <= max(2, 0.25 * io.cycles), (info.cycles, io.cycles)
     xg = xg.cpu().numpy()
     r = p["b"] - h.apply(xg)
     assert np.linalg.norm(r) / np.linalg.norm(p["b"]) <= tol * 1.0001
