@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-f64", action="store_true", help="skip the plain float64 comparison solve")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every V-cycle kernel from the host instead of replaying a captured CUDA graph")
+    ap.add_argument("--grad", action="store_true",
+                    help="also time the adjoint gradients of the Matern loss (and check them by central differences)")
+    ap.add_argument("--grad-n", type=int, default=1 << 16)
+    ap.add_argument("--grad-tol", type=float, default=1e-11)
     ap.add_argument("--skip-square", action="store_true",
                     help="also time the solve with skip_square_levels (no smoothing on square levels)")
     ap.add_argument("--problems", type=int, default=32,
@@ -254,6 +258,46 @@ def uneven_problems(a, pkg, W, torch, stream):
     return out
 
 
+def gradients(a, pkg, W, torch):
+    """The differentiation form on the Matern-3/2 workload (unit cube, l = 0.1, nugget
+    1e-2, leaf 64, 4x4x4 nodes) at --grad-n points: one forward + backward pass of
+    L = 1/2 y^T K^-1 y + 1^T K^-1 b (a three-column mixed-precision solve, the dK/dl
+    sibling and its two-column product), timed, and dL/dl, dL/ds against central
+    differences of the same loss (relative step 1e-4)."""
+    import numpy as np
+    p = W.workload(4, n=a.grad_n)
+    X = torch.from_numpy(p["points"]).cuda()
+    rng = np.random.default_rng(4004)
+    y = torch.from_numpy(rng.standard_normal(p["n"])).cuda()
+    bb = torch.from_numpy(rng.standard_normal(p["n"])).cuda()
+    kw = dict(tol=a.grad_tol, precision="mixed_f32", use_graph=True, max_cycles=400)
+
+    def t64(v, g=False):
+        return torch.tensor(v, dtype=torch.float64, device="cuda", requires_grad=g)
+
+    times = []
+    for _ in range(2):   # the first pass also captures the graphs
+        yt, bt, lt, st = y.clone().requires_grad_(True), bb.clone().requires_grad_(True), t64(0.1, True), \
+            t64(1e-2, True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = pkg.MaternLoss.apply(X, yt, bt, lt, st, **kw)
+        L.backward()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    h = 1e-4
+
+    def loss(l, s):
+        with torch.no_grad():
+            return pkg.MaternLoss.apply(X, y, bb, t64(l), t64(s), **kw).item()
+
+    fd_l = (loss(0.1 * (1 + h), 1e-2) - loss(0.1 * (1 - h), 1e-2)) / (2 * h * 0.1)
+    fd_s = (loss(0.1, 1e-2 * (1 + h)) - loss(0.1, 1e-2 * (1 - h))) / (2 * h * 1e-2)
+    return {"n": p["n"], "kernel": "matern32 l=0.1 nugget=1e-2", "tol": a.grad_tol, "s_loss_and_grads": times[-1],
+            "loss": L.item(), "dL_dl": lt.grad.item(), "dL_ds": st.grad.item(), "fd_dL_dl": fd_l, "fd_dL_ds": fd_s,
+            "rel_err_dl": abs(lt.grad.item() - fd_l) / abs(fd_l), "rel_err_ds": abs(st.grad.item() - fd_s) / abs(fd_s)}
+
+
 # --------------------------------------------------------------------------- our arm
 def main():
     a = parse()
@@ -432,6 +476,7 @@ def main():
     torch.cuda.empty_cache()
 
     problems = uneven_problems(a, pkg, W, torch, stream) if a.problems > 0 else None
+    grads = gradients(a, pkg, W, torch) if a.grad else None
 
     kernel_gbs = kby / kms / 1e6 if kms > 0 else 0.0
     bound = "hbm"
@@ -455,7 +500,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "cycles": cycles, "converged": converged, "relres": infos[-1][2], "relres_check": res_check,
             "matvec": matvec, "f64_solve": f64, "direct_launches": direct, "skip_square_levels": skip, "batched": batched,
-            "problems": problems, "roofline": roof, "gpu_launches": launches,
+            "problems": problems, "gradients": grads, "roofline": roof, "gpu_launches": launches,
             "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 16 * a.n,
                     "d2h_bytes_per_step": 8 * a.n},
             "clocks": clk.summary()}

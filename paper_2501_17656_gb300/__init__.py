@@ -370,14 +370,18 @@ class MaternLoss:
 
     @staticmethod
     def apply(points, y, b, length, nugget, leaf=64, q=4, eta=1.0, tol=1e-12, max_cycles=200,
-              outer="fcg", n_f=1, n_c=40):
+              outer="fcg", n_f=1, n_c=40, precision="f64", use_graph=False):
+        """``precision="mixed_f32"`` runs the V-cycles on an FP32 copy inside the float64
+        outer loop (the solutions still meet ``tol`` in float64)."""
         import torch
 
         class _Fn(torch.autograd.Function):
             @staticmethod
             def forward(ctx, y_, b_, l_, s_):
-                K = H2Matrix(points, "matern32", length=float(l_), nugget=float(s_), leaf=leaf, q=q, eta=eta)
-                kw = dict(tol=tol, max_cycles=max_cycles, outer=outer, n_f=n_f, n_c=n_c)
+                K = H2Matrix(points, "matern32", length=float(l_), nugget=float(s_), leaf=leaf, q=q, eta=eta,
+                             with_f32=(precision == "mixed_f32"))
+                kw = dict(tol=tol, max_cycles=max_cycles, outer=outer, n_f=n_f, n_c=n_c, precision=precision,
+                          use_graph=use_graph)
                 yd = y_.detach().contiguous()
                 ones = torch.ones_like(yd)
                 cols = [yd, b_.detach(), ones] if any(ctx.needs_input_grad) else [yd, b_.detach()]
