@@ -322,10 +322,17 @@ __global__ void k_up_leaf(const BT* __restrict__ UT, int KD, int KC,
 // blocks of k_bsgemv, and one warp streams one transfer with the same lane layout:
 // the upward pass uses the transposed product E'_c^T x_c (reduce-scatter over the
 // lanes that share a column), the downward pass the row product E'_c y_parent.
+//
+// One launch covers up to 3 (upward) or 4 (downward) consecutive tree levels: a CTA
+// owns a subtree (8 clusters of the bottom level going up; one cluster of the top
+// level and its descendants going down), keeps the intermediate coefficients in
+// shared memory and writes every level's coefficients to global memory, since the
+// coupling products and the next launch read them.
+
+// v = E'^T x for one K x K transfer at B (warp-wide; x: K*NR values, any address space)
 template <int K, int FMT, int NR>
-__global__ void __launch_bounds__(256) k_up_blk(const void* __restrict__ Epool,
-                                                const typename Ar<FMT>::vec_t* __restrict__ xch,
-                                                typename Ar<FMT>::vec_t* __restrict__ xpar, int nch) {
+__device__ __forceinline__ void warp_transfer_t(const void* __restrict__ Bv, const typename Ar<FMT>::vec_t* x,
+                                                typename Ar<FMT>::acc_t* v) {
   using A = Ar<FMT>;
   using vec_t = typename A::vec_t;
   using mel_t = typename A::mel_t;
@@ -334,101 +341,20 @@ __global__ void __launch_bounds__(256) k_up_blk(const void* __restrict__ Epool,
   constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
   constexpr int CH = T < LPC ? T : LPC;
   constexpr int V = A::V, P = 8 / V;
-  __shared__ acc_t v[8][K * NR];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c = blockIdx.x * 8 + w;
+  const int lane = threadIdx.x & 31;
   const int rb = 8 * (lane % LPC), cl = lane / LPC;
-  if (c < nch) {
-    vec_t xt[8][NR];
+  vec_t xt[8][NR];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int j = 0; j < NR; ++j) xt[r][j] = xch[((int64_t)c * K + rb + r) * NR + j];
-    const ld_t* B = (const ld_t*)((const char*)Epool + (int64_t)c * K * K * (FMT == FMT_F32 ? 4 : 8));
+    for (int j = 0; j < NR; ++j) xt[r][j] = x[(rb + r) * NR + j];
+  const ld_t* B = (const ld_t*)Bv;
 #pragma unroll 1
-    for (int ch = 0; ch < T / CH; ++ch) {
-      acc_t zc[CH][NR];
+  for (int ch = 0; ch < T / CH; ++ch) {
+    acc_t zc[CH][NR];
 #pragma unroll
-      for (int tt = 0; tt < CH; ++tt) {
-        const int t = ch * CH + tt;
-        mel_t m[8];
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-          ld_t q = __ldg(B + (t * P + k) * 32 + lane);
-          A::decode(q, m + k * V);
-        }
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-          acc_t zz = A::zero();
-#pragma unroll
-          for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r][j]);
-          zc[tt][j] = zz;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NR; ++j) {
-        if (CH == LPC) {
-#pragma unroll
-          for (int h = CH / 2; h >= 1; h >>= 1) {
-            const bool up = (lane & h) != 0;
-#pragma unroll
-            for (int q = 0; q < h; ++q) {
-              acc_t send = up ? zc[q][j] : zc[q + h][j];
-              acc_t keep = up ? zc[q + h][j] : zc[q][j];
-              A::add(keep, A::shfl(send, h));
-              zc[q][j] = keep;
-            }
-          }
-          v[w][(cl + CPP * (ch * CH + (lane & (CH - 1)))) * NR + j] = zc[0][j];
-        } else {
-#pragma unroll
-          for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0][j], A::shfl(zc[0][j], h));
-          if ((lane % LPC) == 0) v[w][(cl + CPP * (ch * CH)) * NR + j] = zc[0][j];
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (c < nch && (w & 1) == 0) {
-    const int p = c >> 1;
-    for (int i = lane; i < K * NR; i += 32) {
-      acc_t s = v[w][i];
-      A::add(s, v[w + 1][i]);
-      xpar[(int64_t)p * K * NR + i] = A::out(s);
-    }
-  }
-}
-
-template <int K, int FMT, int NR>
-__global__ void __launch_bounds__(256) k_down_blk(int slot_base, int ncl,
-                                                  const typename Ar<FMT>::yo_t* __restrict__ yrow,
-                                                  const void* __restrict__ Epool,
-                                                  const typename Ar<FMT>::vec_t* __restrict__ ypar,
-                                                  typename Ar<FMT>::vec_t* __restrict__ yc,
-                                                  double* __restrict__ yout, int64_t ldo) {
-  using A = Ar<FMT>;
-  using vec_t = typename A::vec_t;
-  using mel_t = typename A::mel_t;
-  using acc_t = typename A::acc_t;
-  using ld_t = typename A::ld_t;
-  constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
-  constexpr int V = A::V, P = 8 / V;
-  __shared__ acc_t s[8][K * NR];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c = blockIdx.x * 8 + w;
-  if (c >= ncl) return;
-  const int sl = slot_base + c;
-  if (Epool) {
-    const int rb = 8 * (lane % LPC), cl = lane / LPC;
-    acc_t ya[8][NR];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int j = 0; j < NR; ++j) ya[r][j] = A::zero();
-    const ld_t* B = (const ld_t*)((const char*)Epool + (int64_t)c * K * K * (FMT == FMT_F32 ? 4 : 8));
-    const vec_t* yp = ypar + (int64_t)(c >> 1) * K * NR;
-#pragma unroll 4
-    for (int t = 0; t < T; ++t) {
+    for (int tt = 0; tt < CH; ++tt) {
+      const int t = ch * CH + tt;
       mel_t m[8];
 #pragma unroll
       for (int k = 0; k < P; ++k) {
@@ -437,34 +363,169 @@ __global__ void __launch_bounds__(256) k_down_blk(int slot_base, int ncl,
       }
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
-        const vec_t xv = yp[(cl + CPP * t) * NR + j];
+        acc_t zz = A::zero();
 #pragma unroll
-        for (int r = 0; r < 8; ++r) A::fma(ya[r][j], m[r], xv);
+        for (int r = 0; r < 8; ++r) A::fma(zz, m[r], xt[r][j]);
+        zc[tt][j] = zz;
       }
     }
 #pragma unroll
-    for (int h = LPC; h < 32; h <<= 1)
+    for (int j = 0; j < NR; ++j) {
+      if (CH == LPC) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
+        for (int h = CH / 2; h >= 1; h >>= 1) {
+          const bool up = (lane & h) != 0;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) A::add(ya[r][j], A::shfl(ya[r][j], h));
-    if (lane < LPC)
+          for (int q = 0; q < h; ++q) {
+            acc_t send = up ? zc[q][j] : zc[q + h][j];
+            acc_t keep = up ? zc[q + h][j] : zc[q][j];
+            A::add(keep, A::shfl(send, h));
+            zc[q][j] = keep;
+          }
+        }
+        v[(cl + CPP * (ch * CH + (lane & (CH - 1)))) * NR + j] = zc[0][j];
+      } else {
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int j = 0; j < NR; ++j) s[w][(rb + r) * NR + j] = ya[r][j];
-    __syncwarp();
-  }
-  for (int i = lane; i < K * NR; i += 32) {
-    acc_t acc = A::from_d((double)yrow[(int64_t)sl * K * NR + i]);
-    if (Epool) A::add(acc, s[w][i]);
-    vec_t o = A::out(acc);
-    if (yout) {
-      const int a = i / NR, j = i % NR;
-      yout[(int64_t)c * K + a + j * ldo] = A::to_d(o);
-    } else {
-      yc[(int64_t)sl * K * NR + i] = o;
+        for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0][j], A::shfl(zc[0][j], h));
+        if ((lane % LPC) == 0) v[(cl + CPP * (ch * CH)) * NR + j] = zc[0][j];
+      }
     }
+  }
+}
+
+// s = E' y for one K x K transfer at B (warp-wide; y: K*NR values, any address space)
+template <int K, int FMT, int NR>
+__device__ __forceinline__ void warp_transfer(const void* __restrict__ Bv, const typename Ar<FMT>::vec_t* y,
+                                              typename Ar<FMT>::acc_t* s) {
+  using A = Ar<FMT>;
+  using vec_t = typename A::vec_t;
+  using mel_t = typename A::mel_t;
+  using acc_t = typename A::acc_t;
+  using ld_t = typename A::ld_t;
+  constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
+  constexpr int V = A::V, P = 8 / V;
+  const int lane = threadIdx.x & 31;
+  const int rb = 8 * (lane % LPC), cl = lane / LPC;
+  acc_t ya[8][NR];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) ya[r][j] = A::zero();
+  const ld_t* B = (const ld_t*)Bv;
+#pragma unroll 4
+  for (int t = 0; t < T; ++t) {
+    mel_t m[8];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      ld_t q = __ldg(B + (t * P + k) * 32 + lane);
+      A::decode(q, m + k * V);
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const vec_t xv = y[(cl + CPP * t) * NR + j];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) A::fma(ya[r][j], m[r], xv);
+    }
+  }
+#pragma unroll
+  for (int h = LPC; h < 32; h <<= 1)
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) A::add(ya[r][j], A::shfl(ya[r][j], h));
+  if (lane < LPC)
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) s[(rb + r) * NR + j] = ya[r][j];
+}
+
+// Levels of one pass launch: step k works on tree level `lev[k]`.
+struct PassLevels {
+  const void* E[4];   // transfer pool of the (child) clusters of step k (nullptr: top level, no parent)
+  void* out[4];       // up: parent coefficients of step k; down: coefficients of step k's clusters
+  int slot[4];        // down: first slot of step k's level (row buffer index)
+  int n[4];           // clusters of step k's level
+};
+
+// Upward pass over `steps` levels: step k maps the children (level lc - k) of this
+// CTA's subtree to their parents. x_bottom: coefficients of level lc.
+template <int K, int FMT, int NR>
+__global__ void __launch_bounds__(256) k_up_multi(PassLevels pl, int steps,
+                                                  const typename Ar<FMT>::vec_t* __restrict__ xbottom) {
+  using A = Ar<FMT>;
+  using vec_t = typename A::vec_t;
+  using acc_t = typename A::acc_t;
+  constexpr size_t kBlk = (size_t)K * K * (FMT == FMT_F32 ? 4 : 8);
+  __shared__ acc_t v[8][K * NR];
+  __shared__ vec_t xin[4][K * NR];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < steps; ++k) {
+    const int per = 8 >> k;                 // children of this CTA at step k
+    const int c = blockIdx.x * per + w;     // child index within its level
+    if (w < per && c < pl.n[k]) {
+      const vec_t* x = (k == 0) ? xbottom + (int64_t)c * K * NR : xin[w];
+      warp_transfer_t<K, FMT, NR>((const char*)pl.E[k] + (size_t)c * kBlk, x, v[w]);
+    }
+    __syncthreads();
+    if (w < per && (w & 1) == 0 && c < pl.n[k]) {
+      vec_t* xo = (vec_t*)pl.out[k] + (int64_t)(c >> 1) * K * NR;
+      for (int i = lane; i < K * NR; i += 32) {
+        acc_t t = v[w][i];
+        A::add(t, v[w + 1][i]);
+        const vec_t o = A::out(t);
+        xo[i] = o;
+        xin[w >> 1][i] = o;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Downward pass over `steps` levels from this CTA's top cluster (level lt): step k
+// forms y_c = yrow_c + E'_c y_parent(c) for the 2^k descendants at level lt + k
+// (no transfer term at the coupling top level). ypar: coefficients of level lt - 1.
+// On the last step of the last launch the result goes to yout (float64, column j at
+// yout + j * ldo) instead of the coefficient buffer, when yout is given.
+template <int K, int FMT, int NR>
+__global__ void __launch_bounds__(256) k_down_multi(PassLevels pl, int steps,
+                                                    const typename Ar<FMT>::yo_t* __restrict__ yrow,
+                                                    const typename Ar<FMT>::vec_t* __restrict__ ypar,
+                                                    double* __restrict__ yout, int64_t ldo) {
+  using A = Ar<FMT>;
+  using vec_t = typename A::vec_t;
+  using acc_t = typename A::acc_t;
+  constexpr size_t kBlk = (size_t)K * K * (FMT == FMT_F32 ? 4 : 8);
+  __shared__ acc_t sv[8][K * NR];
+  __shared__ vec_t ys[8][K * NR];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < steps; ++k) {
+    const int per = 1 << k;                 // clusters of this CTA at step k
+    const int c = blockIdx.x * per + w;     // cluster index within its level
+    const bool mine = w < per && c < pl.n[k];
+    if (mine && pl.E[k]) {
+      const vec_t* yp = (k == 0) ? ypar + (int64_t)(c >> 1) * K * NR : ys[w >> 1];
+      warp_transfer<K, FMT, NR>((const char*)pl.E[k] + (size_t)c * kBlk, yp, sv[w]);
+    }
+    __syncthreads();   // every parent value of this step has been read
+    if (mine) {
+      const int sl = pl.slot[k] + c;
+      const bool last = (k == steps - 1) && yout;
+      vec_t* yc = (vec_t*)pl.out[k] + (int64_t)c * K * NR;
+      for (int i = lane; i < K * NR; i += 32) {
+        acc_t acc = A::from_d((double)yrow[(int64_t)sl * K * NR + i]);
+        if (pl.E[k]) A::add(acc, sv[w][i]);
+        const vec_t o = A::out(acc);
+        if (last) {
+          const int a = i / NR, j = i % NR;
+          yout[(int64_t)c * K + a + j * ldo] = A::to_d(o);
+        } else {
+          yc[i] = o;
+          ys[w][i] = o;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -746,30 +807,62 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
   }
 }
 
+// Upward pass from tree level `lb` (coefficients at xc + cslot(lb)) to level `ltop`:
+// children of level l + 1 -> parents of level l, up to 3 levels per launch.
 template <int FMT, int NR>
-static void launch_up(const void* Epool, int KC, const void* xch, void* xpar, int nch, cudaStream_t s) {
+static void pass_up(const Matrix& M, const char* epool, size_t eb, void* xc, int lb, int ltop, cudaStream_t s) {
   using vt = typename Ar<FMT>::vec_t;
-  int grid = ceil_div(nch, 8);
-  switch (KC) {
-    case 16: { k_up_blk<16, FMT, NR><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
-    case 32: { k_up_blk<32, FMT, NR><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
-    default: { k_up_blk<64, FMT, NR><<<grid, 256, 0, s>>>(Epool, (const vt*)xch, (vt*)xpar, nch); ::h2mg::count_launch(); } break;
+  const int KC = M.KC;
+  auto cslot = [&](int ell) { return (vt*)xc + (size_t)M.slot0(ell) * KC * NR; };
+  for (int lc = lb; lc > ltop;) {
+    const int steps = std::min(3, lc - ltop);
+    PassLevels pl{};
+    for (int k = 0; k < steps; ++k) {
+      pl.E[k] = epool + (size_t)M.slot0(lc - k) * KC * KC * eb;
+      pl.out[k] = cslot(lc - k - 1);
+      pl.n[k] = 1 << (lc - k);
+    }
+    const int grid = ceil_div(1 << lc, 8);
+    switch (KC) {
+      case 16: { k_up_multi<16, FMT, NR><<<grid, 256, 0, s>>>(pl, steps, cslot(lc)); ::h2mg::count_launch(); } break;
+      case 32: { k_up_multi<32, FMT, NR><<<grid, 256, 0, s>>>(pl, steps, cslot(lc)); ::h2mg::count_launch(); } break;
+      default: { k_up_multi<64, FMT, NR><<<grid, 256, 0, s>>>(pl, steps, cslot(lc)); ::h2mg::count_launch(); } break;
+    }
+    H2_LAUNCH_CHECK();
+    lc -= steps;
   }
-  H2_LAUNCH_CHECK();
 }
 
+// Downward pass from the coupling top level ts to level `lbot`, up to 4 levels per
+// launch; the last level goes to yout (when given) instead of the coefficient buffer.
 template <int FMT, int NR>
-static void launch_down(int slot_base, int KC, int ncl, const void* yrow, const void* Epool, const void* ypar,
-                        void* yc, double* yout, int64_t ldo, cudaStream_t s) {
+static void pass_down(const Matrix& M, const char* epool, size_t eb, const void* yrow, void* yc, int ts, int lbot,
+                      double* yout, int64_t ldo, cudaStream_t s) {
   using vt = typename Ar<FMT>::vec_t;
   using yt = typename Ar<FMT>::yo_t;
-  int grid = ceil_div(ncl, 8);
-  switch (KC) {
-    case 16: { k_down_blk<16, FMT, NR><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout, ldo); ::h2mg::count_launch(); } break;
-    case 32: { k_down_blk<32, FMT, NR><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout, ldo); ::h2mg::count_launch(); } break;
-    default: { k_down_blk<64, FMT, NR><<<grid, 256, 0, s>>>(slot_base, ncl, (const yt*)yrow, Epool, (const vt*)ypar, (vt*)yc, yout, ldo); ::h2mg::count_launch(); } break;
+  const int KC = M.KC;
+  auto cslot = [&](int ell) { return (vt*)yc + (size_t)M.slot0(ell) * KC * NR; };
+  for (int lt = ts; lt <= lbot;) {
+    const int steps = std::min(4, lbot - lt + 1);
+    PassLevels pl{};
+    for (int k = 0; k < steps; ++k) {
+      const int ell = lt + k;
+      pl.E[k] = ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr;
+      pl.out[k] = cslot(ell);
+      pl.slot[k] = M.slot0(ell);
+      pl.n[k] = 1 << ell;
+    }
+    const vt* ypar = lt > ts ? cslot(lt - 1) : nullptr;
+    double* yo = (lt + steps - 1 == lbot) ? yout : nullptr;
+    const int grid = 1 << lt;
+    switch (KC) {
+      case 16: { k_down_multi<16, FMT, NR><<<grid, 256, 0, s>>>(pl, steps, (const yt*)yrow, ypar, yo, ldo); ::h2mg::count_launch(); } break;
+      case 32: { k_down_multi<32, FMT, NR><<<grid, 256, 0, s>>>(pl, steps, (const yt*)yrow, ypar, yo, ldo); ::h2mg::count_launch(); } break;
+      default: { k_down_multi<64, FMT, NR><<<grid, 256, 0, s>>>(pl, steps, (const yt*)yrow, ypar, yo, ldo); ::h2mg::count_launch(); } break;
+    }
+    H2_LAUNCH_CHECK();
+    lt += steps;
   }
-  H2_LAUNCH_CHECK();
 }
 
 // y = A_i x for NR columns (x, y column-major with leading dimensions ldx, ldy).
@@ -798,17 +891,12 @@ static void apply_impl(Matrix& M, int i, const double* x, int64_t ldx, double* y
     if (ts >= 0) {
       { k_up_leaf<FMT, BT, NR><<<1 << L, std::max(KC, 32), 0, s>>>(UT, KD, KC, xp, xc + cslot(L)); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
-      for (int ell = L - 1; ell >= ts; --ell)
-        launch_up<FMT, NR>(epool + (size_t)M.slot0(ell + 1) * KC * KC * eb, KC, xc + cslot(ell + 1), xc + cslot(ell),
-                           1 << (ell + 1), s);
+      pass_up<FMT, NR>(M, epool, eb, xc, L, ts, s);
     }
     launch_bsgemv<FMT, NR>(M, M.opD, f32, xp, yp, s);
     if (ts >= 0) {
       launch_bsgemv<FMT, NR>(M, M.opC[1], f32, xc, yr, s);
-      for (int ell = ts; ell <= L; ++ell)
-        launch_down<FMT, NR>(M.slot0(ell), KC, 1 << ell, yr,
-                             ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr,
-                             ell > ts ? yc + cslot(ell - 1) : nullptr, yc, nullptr, 0, s);
+      pass_down<FMT, NR>(M, epool, eb, yr, yc, ts, L, nullptr, 0, s);
     }
     { k_leaf_final<FMT, BT, NR><<<1 << L, std::max(KD, 32), 0, s>>>(
         KD, KC, yp, ts >= 0 ? U : nullptr, ts >= 0 ? yc + cslot(L) : nullptr, M.d_leafoff, M.d_perm, y, ldy);
@@ -820,14 +908,9 @@ static void apply_impl(Matrix& M, int i, const double* x, int64_t ldx, double* y
   const int64_t nm = (int64_t)(1 << m) * KC;
   { k_coef_in<FMT, NR><<<ceil_div(nm, 256), 256, 0, s>>>(x, ldx, nm, xc + cslot(m)); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
-  for (int ell = m - 1; ell >= ts; --ell)
-    launch_up<FMT, NR>(epool + (size_t)M.slot0(ell + 1) * KC * KC * eb, KC, xc + cslot(ell + 1), xc + cslot(ell),
-                       1 << (ell + 1), s);
+  pass_up<FMT, NR>(M, epool, eb, xc, m, ts, s);
   launch_bsgemv<FMT, NR>(M, M.opC[i], f32, xc, yr, s);
-  for (int ell = ts; ell <= m; ++ell)
-    launch_down<FMT, NR>(M.slot0(ell), KC, 1 << ell, yr,
-                         ell > ts ? epool + (size_t)M.slot0(ell) * KC * KC * eb : nullptr,
-                         ell > ts ? yc + cslot(ell - 1) : nullptr, yc, ell == m ? y : nullptr, ldy, s);
+  pass_down<FMT, NR>(M, epool, eb, yr, yc, ts, m, y, ldy, s);
 }
 
 template <int FMT, class BT>
