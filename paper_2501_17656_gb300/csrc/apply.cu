@@ -329,17 +329,20 @@ __global__ void k_up_leaf(const BT* __restrict__ UT, int KD, int KC,
 // shared memory and writes every level's coefficients to global memory, since the
 // coupling products and the next launch read them.
 
-// v = E'^T x for one K x K transfer at B (warp-wide; x: K*NR values, any address space)
-template <int K, int FMT, int NR>
+// v = E'^T x over the TPW tiles starting at tile t0 of one K x K transfer at B
+// (warp-wide; x: K*NR values, any address space). A tile covers CPP whole columns of
+// E', so the tiles of one transfer can be split over several warps, each writing the
+// outputs of its own columns.
+template <int K, int FMT, int NR, int TPW>
 __device__ __forceinline__ void warp_transfer_t(const void* __restrict__ Bv, const typename Ar<FMT>::vec_t* x,
-                                                typename Ar<FMT>::acc_t* v) {
+                                                typename Ar<FMT>::acc_t* v, int t0) {
   using A = Ar<FMT>;
   using vec_t = typename A::vec_t;
   using mel_t = typename A::mel_t;
   using acc_t = typename A::acc_t;
   using ld_t = typename A::ld_t;
-  constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
-  constexpr int CH = T < LPC ? T : LPC;
+  constexpr int LPC = K / 8, CPP = 32 / LPC;
+  constexpr int CH = TPW < LPC ? TPW : LPC;
   constexpr int V = A::V, P = 8 / V;
   const int lane = threadIdx.x & 31;
   const int rb = 8 * (lane % LPC), cl = lane / LPC;
@@ -350,11 +353,11 @@ __device__ __forceinline__ void warp_transfer_t(const void* __restrict__ Bv, con
     for (int j = 0; j < NR; ++j) xt[r][j] = x[(rb + r) * NR + j];
   const ld_t* B = (const ld_t*)Bv;
 #pragma unroll 1
-  for (int ch = 0; ch < T / CH; ++ch) {
+  for (int ch = 0; ch < TPW / CH; ++ch) {
     acc_t zc[CH][NR];
 #pragma unroll
     for (int tt = 0; tt < CH; ++tt) {
-      const int t = ch * CH + tt;
+      const int t = t0 + ch * CH + tt;
       mel_t m[8];
 #pragma unroll
       for (int k = 0; k < P; ++k) {
@@ -371,38 +374,53 @@ __device__ __forceinline__ void warp_transfer_t(const void* __restrict__ Bv, con
     }
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      if (CH == LPC) {
+      // butterfly over the CH tiles (lane keeps tile lane & (CH-1)), then the rest of
+      // the LPC lanes that share a column
 #pragma unroll
-        for (int h = CH / 2; h >= 1; h >>= 1) {
-          const bool up = (lane & h) != 0;
+      for (int h = CH / 2; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
 #pragma unroll
-          for (int q = 0; q < h; ++q) {
-            acc_t send = up ? zc[q][j] : zc[q + h][j];
-            acc_t keep = up ? zc[q + h][j] : zc[q][j];
-            A::add(keep, A::shfl(send, h));
-            zc[q][j] = keep;
-          }
+        for (int q = 0; q < h; ++q) {
+          acc_t send = up ? zc[q][j] : zc[q + h][j];
+          acc_t keep = up ? zc[q + h][j] : zc[q][j];
+          A::add(keep, A::shfl(send, h));
+          zc[q][j] = keep;
         }
-        v[(cl + CPP * (ch * CH + (lane & (CH - 1)))) * NR + j] = zc[0][j];
-      } else {
-#pragma unroll
-        for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0][j], A::shfl(zc[0][j], h));
-        if ((lane % LPC) == 0) v[(cl + CPP * (ch * CH)) * NR + j] = zc[0][j];
       }
+#pragma unroll
+      for (int h = CH; h < LPC; h <<= 1) A::add(zc[0][j], A::shfl(zc[0][j], h));
+      if ((lane % LPC) < CH) v[(cl + CPP * (t0 + ch * CH + (lane & (CH - 1)))) * NR + j] = zc[0][j];
     }
   }
 }
 
-// s = E' y for one K x K transfer at B (warp-wide; y: K*NR values, any address space)
+// Splits one transfer's T tiles over `wpb` warps (a power of two): warp `sub` takes
+// T / wpb consecutive tiles (warps beyond T do nothing).
+template <int K, int FMT, int NR>
+__device__ __forceinline__ void warp_transfer_t_part(const void* B, const typename Ar<FMT>::vec_t* x,
+                                                     typename Ar<FMT>::acc_t* v, int wpb, int sub) {
+  constexpr int T = K * K / 256;
+  const int w = wpb < T ? wpb : T;
+  if (sub >= w) return;
+  const int tpw = T / w;
+  if constexpr (T >= 16) if (tpw == 16) { warp_transfer_t<K, FMT, NR, 16>(B, x, v, 0); return; }
+  if constexpr (T >= 8) if (tpw == 8) { warp_transfer_t<K, FMT, NR, 8>(B, x, v, sub * 8); return; }
+  if constexpr (T >= 4) if (tpw == 4) { warp_transfer_t<K, FMT, NR, 4>(B, x, v, sub * 4); return; }
+  if constexpr (T >= 2) if (tpw == 2) { warp_transfer_t<K, FMT, NR, 2>(B, x, v, sub * 2); return; }
+  warp_transfer_t<K, FMT, NR, 1>(B, x, v, sub);
+}
+
+// s = rows of E' y over the tiles [t0, t1) of one K x K transfer at B (warp-wide;
+// y: K*NR values, any address space); partial sums over those tiles' columns.
 template <int K, int FMT, int NR>
 __device__ __forceinline__ void warp_transfer(const void* __restrict__ Bv, const typename Ar<FMT>::vec_t* y,
-                                              typename Ar<FMT>::acc_t* s) {
+                                              typename Ar<FMT>::acc_t* s, int t0, int t1) {
   using A = Ar<FMT>;
   using vec_t = typename A::vec_t;
   using mel_t = typename A::mel_t;
   using acc_t = typename A::acc_t;
   using ld_t = typename A::ld_t;
-  constexpr int LPC = K / 8, CPP = 32 / LPC, T = K * K / 256;
+  constexpr int LPC = K / 8, CPP = 32 / LPC;
   constexpr int V = A::V, P = 8 / V;
   const int lane = threadIdx.x & 31;
   const int rb = 8 * (lane % LPC), cl = lane / LPC;
@@ -413,7 +431,7 @@ __device__ __forceinline__ void warp_transfer(const void* __restrict__ Bv, const
     for (int j = 0; j < NR; ++j) ya[r][j] = A::zero();
   const ld_t* B = (const ld_t*)Bv;
 #pragma unroll 4
-  for (int t = 0; t < T; ++t) {
+  for (int t = t0; t < t1; ++t) {
     mel_t m[8];
 #pragma unroll
     for (int k = 0; k < P; ++k) {
@@ -449,7 +467,8 @@ struct PassLevels {
 };
 
 // Upward pass over `steps` levels: step k maps the children (level lc - k) of this
-// CTA's subtree to their parents. x_bottom: coefficients of level lc.
+// CTA's subtree to their parents. x_bottom: coefficients of level lc. At step k the
+// 8 >> k children of the CTA share its 8 warps (1 << k warps per transfer).
 template <int K, int FMT, int NR>
 __global__ void __launch_bounds__(256) k_up_multi(PassLevels pl, int steps,
                                                   const typename Ar<FMT>::vec_t* __restrict__ xbottom) {
@@ -459,23 +478,25 @@ __global__ void __launch_bounds__(256) k_up_multi(PassLevels pl, int steps,
   constexpr size_t kBlk = (size_t)K * K * (FMT == FMT_F32 ? 4 : 8);
   __shared__ acc_t v[8][K * NR];
   __shared__ vec_t xin[4][K * NR];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5;
   for (int k = 0; k < steps; ++k) {
     const int per = 8 >> k;                 // children of this CTA at step k
-    const int c = blockIdx.x * per + w;     // child index within its level
-    if (w < per && c < pl.n[k]) {
-      const vec_t* x = (k == 0) ? xbottom + (int64_t)c * K * NR : xin[w];
-      warp_transfer_t<K, FMT, NR>((const char*)pl.E[k] + (size_t)c * kBlk, x, v[w]);
+    const int b = w >> k, sub = w & ((1 << k) - 1);
+    const int c = blockIdx.x * per + b;     // child index within its level
+    if (c < pl.n[k]) {
+      const vec_t* x = (k == 0) ? xbottom + (int64_t)c * K * NR : xin[b];
+      warp_transfer_t_part<K, FMT, NR>((const char*)pl.E[k] + (size_t)c * kBlk, x, v[b], 1 << k, sub);
     }
     __syncthreads();
-    if (w < per && (w & 1) == 0 && c < pl.n[k]) {
-      vec_t* xo = (vec_t*)pl.out[k] + (int64_t)(c >> 1) * K * NR;
-      for (int i = lane; i < K * NR; i += 32) {
-        acc_t t = v[w][i];
-        A::add(t, v[w + 1][i]);
+    for (int idx = threadIdx.x; idx < (per / 2) * K * NR; idx += blockDim.x) {
+      const int pb = idx / (K * NR), i = idx % (K * NR);
+      const int c0 = blockIdx.x * per + 2 * pb;
+      if (c0 < pl.n[k]) {
+        acc_t t = v[2 * pb][i];
+        A::add(t, v[2 * pb + 1][i]);
         const vec_t o = A::out(t);
-        xo[i] = o;
-        xin[w >> 1][i] = o;
+        ((vec_t*)pl.out[k])[(int64_t)(c0 >> 1) * K * NR + i] = o;
+        xin[pb][i] = o;
       }
     }
     __syncthreads();
@@ -484,7 +505,8 @@ __global__ void __launch_bounds__(256) k_up_multi(PassLevels pl, int steps,
 
 // Downward pass over `steps` levels from this CTA's top cluster (level lt): step k
 // forms y_c = yrow_c + E'_c y_parent(c) for the 2^k descendants at level lt + k
-// (no transfer term at the coupling top level). ypar: coefficients of level lt - 1.
+// (no transfer term at the coupling top level), the CTA's 8 warps sharing each
+// transfer's tiles (8 >> k warps per transfer). ypar: coefficients of level lt - 1.
 // On the last step of the last launch the result goes to yout (float64, column j at
 // yout + j * ldo) instead of the coefficient buffer, when yout is given.
 template <int K, int FMT, int NR>
@@ -496,33 +518,37 @@ __global__ void __launch_bounds__(256) k_down_multi(PassLevels pl, int steps,
   using vec_t = typename A::vec_t;
   using acc_t = typename A::acc_t;
   constexpr size_t kBlk = (size_t)K * K * (FMT == FMT_F32 ? 4 : 8);
+  constexpr int T = K * K / 256;
   __shared__ acc_t sv[8][K * NR];
   __shared__ vec_t ys[8][K * NR];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5;
   for (int k = 0; k < steps; ++k) {
-    const int per = 1 << k;                 // clusters of this CTA at step k
-    const int c = blockIdx.x * per + w;     // cluster index within its level
-    const bool mine = w < per && c < pl.n[k];
-    if (mine && pl.E[k]) {
-      const vec_t* yp = (k == 0) ? ypar + (int64_t)(c >> 1) * K * NR : ys[w >> 1];
-      warp_transfer<K, FMT, NR>((const char*)pl.E[k] + (size_t)c * kBlk, yp, sv[w]);
+    const int per = 1 << k;                       // clusters of this CTA at step k
+    const int wpb = 8 >> k;                       // warps per transfer
+    const int wpe = wpb < T ? wpb : T;            // of which hold tiles
+    const int b = w / wpb, sub = w % wpb;
+    const int c = blockIdx.x * per + b;           // cluster index within its level
+    if (pl.E[k] && c < pl.n[k] && sub < wpe) {
+      const vec_t* yp = (k == 0) ? ypar + (int64_t)(c >> 1) * K * NR : ys[b >> 1];
+      const int tpw = T / wpe;
+      warp_transfer<K, FMT, NR>((const char*)pl.E[k] + (size_t)c * kBlk, yp, sv[w], sub * tpw, (sub + 1) * tpw);
     }
-    __syncthreads();   // every parent value of this step has been read
-    if (mine) {
-      const int sl = pl.slot[k] + c;
-      const bool last = (k == steps - 1) && yout;
-      vec_t* yc = (vec_t*)pl.out[k] + (int64_t)c * K * NR;
-      for (int i = lane; i < K * NR; i += 32) {
-        acc_t acc = A::from_d((double)yrow[(int64_t)sl * K * NR + i]);
-        if (pl.E[k]) A::add(acc, sv[w][i]);
-        const vec_t o = A::out(acc);
-        if (last) {
-          const int a = i / NR, j = i % NR;
-          yout[(int64_t)c * K + a + j * ldo] = A::to_d(o);
-        } else {
-          yc[i] = o;
-          ys[w][i] = o;
-        }
+    __syncthreads();   // every parent value and partial of this step is in place
+    const bool last = (k == steps - 1) && yout;
+    for (int idx = threadIdx.x; idx < per * K * NR; idx += blockDim.x) {
+      const int bb = idx / (K * NR), i = idx % (K * NR);
+      const int cc = blockIdx.x * per + bb;
+      if (cc >= pl.n[k]) continue;
+      acc_t acc = A::from_d((double)yrow[(int64_t)(pl.slot[k] + cc) * K * NR + i]);
+      if (pl.E[k])
+        for (int q = 0; q < wpe; ++q) A::add(acc, sv[bb * wpb + q][i]);
+      const vec_t o = A::out(acc);
+      if (last) {
+        const int a = i / NR, j = i % NR;
+        yout[(int64_t)cc * K + a + j * ldo] = A::to_d(o);
+      } else {
+        ((vec_t*)pl.out[k])[(int64_t)cc * K * NR + i] = o;
+        ys[bb][i] = o;
       }
     }
     __syncthreads();
