@@ -10,9 +10,10 @@
 // or every coupling level at once: one CTA per block row, each warp streams whole
 // K x K blocks (swizzled so that every warp load is one contiguous 512 B segment),
 // and each block is used twice -- y_t += B x_s for its row and, for s != t, the
-// transposed product B^T x_t for its column, written to the entry's scratch row.
-// The downward pass (k_down_final) gathers those scratch rows, adds the row
-// results and the transfer from the parent, and converts the finest level out.
+// transposed product B^T x_t for its column, both added atomically into a zeroed row
+// buffer. The upward pass (k_up_leaf, k_up_multi) forms the cluster coefficients of
+// every level; the downward pass (k_down_multi) adds the transfer from the parent to
+// each level's row results and writes the finest level out (k_leaf_final at i = 1).
 //
 // Arithmetic per block format: F64 (DFMA), DF (double-float on the FP32 pipes: the
 // error-free products/sums of Dekker and Knuth), F32 (FP32 FMA). Vectors inside the
