@@ -384,8 +384,31 @@ def main():
             by = Am.query("APPLY_BYTES", 1) * (0.5 if prec == "mixed_f32" else 1.0)
             matvec[prec] = {"n": a.matvec_n, "ms": ms, "GBs": by / ms / 1e6,
                             "kernel_GBs": kby / kms / 1e6 if kms > 0 else None}
+            if prec == "f64":
+                y64 = yv.clone()
         Am.close()
-        del Am, Xm, xv, yv
+        del Am
+        torch.cuda.empty_cache()
+        # the same matrix stored as double-float pairs: float64-class products on the
+        # FP32 pipes at HBM speed
+        Ad = pkg.H2Matrix(Xm, "gaussian", length=a.length, nugget=a.nugget, leaf=64, q=4, eta=1.0, storage="df64")
+        Ad.apply_level(1, xv, "f64", y=yv)
+        torch.cuda.synchronize()
+        Ad.profile(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            Ad.apply_level(1, xv, "f64", y=yv)
+        e1.record()
+        torch.cuda.synchronize()
+        nl, kms, kby = Ad.profile(0)
+        ms = e0.elapsed_time(e1) / 5
+        by = Ad.query("APPLY_BYTES", 1)
+        matvec["df64"] = {"n": a.matvec_n, "ms": ms, "GBs": by / ms / 1e6,
+                          "kernel_GBs": kby / kms / 1e6 if kms > 0 else None,
+                          "rel_diff_vs_f64": float(((yv - y64).norm() / y64.norm()).item())}
+        Ad.close()
+        del Ad, Xm, xv, yv, y64
         torch.cuda.empty_cache()
 
     # ---- the solve workload
