@@ -55,7 +55,7 @@ def test_build_rejects_bad_arguments_without_cuda(lib):
         (pts.ctypes.data, 100, 2, k, pkg._BuildOpts(32, 3, -1.0, 0, 0, -1)),  # eta
         (pts.ctypes.data, 100, 2, k, pkg._BuildOpts(32, 3, 1.0, 7, 0, -1)),   # storage
         (pts.ctypes.data, 100, 2, pkg._Kernel(0, -0.1, 0.0, 2, None, None), good),  # length
-        (pts.ctypes.data, 100, 2, pkg._Kernel(3, 1.0, 0.0, 2, None, None), good),   # laplace w/o diag
+        (pts.ctypes.data, 100, 2, pkg._Kernel(3, 1.0, 0.0, 2, None, None), good),   # single layer without areas or diagonal
         (pts.ctypes.data, 100, 2, pkg._Kernel(9, 1.0, 0.0, 2, None, None), good),   # kind
     ]
     for (p, n, d, kk, o) in cases:
@@ -70,3 +70,26 @@ def test_null_handles(lib):
     v = ctypes.c_int64()
     assert lib.h2mg_query(None, 0, 0, ctypes.byref(v)) == 1
     assert lib.h2mg_apply(None, None, None, 1, 1, None) == 1
+    assert lib.h2mg_apply_noalloc(None, None, None, None) == 1
+    assert lib.h2mg_profile(None, 1, None, None, None) == 1
+    out = ctypes.c_double()
+    assert lib.h2mg_dot(None, None, 4, ctypes.byref(out), None) == 1
+    import paper_2501_17656_gb300 as pkg
+    k = pkg._Kernel(5, 0.1, 0.0, 2, None, None)
+    h = ctypes.c_void_p()
+    assert lib.h2mg_build_sibling(None, ctypes.byref(k), None, ctypes.byref(h)) == 1 and not h.value
+
+
+def test_batched_solve_rejects_bad_arguments_without_cuda(lib):
+    import paper_2501_17656_gb300 as pkg
+    o = pkg.H2Matrix._opts()
+    infos = (pkg.SolveInfo * 2)()
+    arr = ctypes.c_void_p * 2
+    nul = arr(None, None)
+    assert lib.h2mg_solve_batched(0, nul, nul, nul, ctypes.byref(o), infos, None) == 1      # no problems
+    assert lib.h2mg_solve_batched(2, None, nul, nul, ctypes.byref(o), infos, None) == 1     # null list
+    assert lib.h2mg_solve_batched(2, nul, nul, nul, ctypes.byref(o), infos, None) == 1      # null handles
+    bad = pkg.H2Matrix._opts(max_cycles=-1)
+    assert lib.h2mg_solve_batched(2, nul, nul, nul, ctypes.byref(bad), infos, None) == 1
+    assert lib.h2mg_last_error().decode()
+
