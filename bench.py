@@ -9,7 +9,7 @@ iteration. The matrix build is timed separately and reported as ``build_s``.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank solves its own problem (replicas; the solve does not
-shard in this build); ``value`` is the sum over ranks of solves / max time.
+shard across GPUs); ``value`` is the sum over ranks of solves / max time.
 """
 from __future__ import annotations
 

@@ -46,7 +46,7 @@ typedef enum {
     H2MG_ERR_NOT_CONVERGED = 5,  /* max_cycles reached above tol (info is filled)      */
     H2MG_ERR_NAN = 6,            /* a NaN/Inf appeared in the input or the residual     */
     H2MG_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up                  */
-    H2MG_ERR_UNSUPPORTED = 8     /* valid request outside what this build implements    */
+    H2MG_ERR_UNSUPPORTED = 8     /* valid request outside what the library implements   */
 } h2mg_status;
 
 /* Kernel functions k(x, y), r = |x - y| (Sec. 4: eqs. a_gau, a_exp; Sec. 4.3). */
@@ -232,8 +232,8 @@ h2mg_status h2mg_export(h2mg_matrix A, int what, int arg, void* buf, int64_t cap
 h2mg_status h2mg_apply_level(h2mg_matrix A, int level, int precision, const double* x,
                              double* y, void* stream);
 
-/* e = dir_sol(A_l, r) by the Cholesky factor of the coarsest operator
- * (Sec. 3.3, Algorithm 1 line dir_sol). Vectors as for h2mg_apply_level at i = l. */
+/* e = dir_sol(A_l, r) through A_l^{-1}, formed at build from the Cholesky factor of
+ * the coarsest operator (Sec. 3.3, the dir_sol step of Algorithm 1). Vectors as for h2mg_apply_level at i = l. */
 h2mg_status h2mg_coarse_solve(h2mg_matrix A, const double* r, double* e, void* stream);
 
 /* One call of the smoother Iter(A_i, f, x0) = n iterations of CG (Sec. 3.3) on
