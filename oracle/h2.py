@@ -288,13 +288,25 @@ class H2Matrix:
 
     Parameters mirror the paper's problem statement: points, kernel, leaf size,
     interpolation order q (rank k = q^d) and admissibility parameter eta.
+
+    ``basis`` selects how the nested bases are made before orthonormalisation:
+    ``"chebyshev"`` (tensor interpolation with q nodes per axis, rank q^d), or
+    ``"skeleton"`` (recursive skeletonization to the relative tolerance ``tol`` with
+    ranks of at most ``rank_max``, see ``oracle.skeleton``; the paper's matrices are
+    built by such a tolerance-driven method, Sec. 4.1). Both yield the same
+    ingredients -- leaf basis, child-to-parent transfers, coupling points -- and
+    the same orthonormalisation and couplings S = R_tau S^0 R_sigma^T follow.
     """
 
     def __init__(self, points, kspec: KernelSpec, leaf: int, q: int, eta: float,
-                 tree: ClusterTree | None = None, partition=None):
+                 tree: ClusterTree | None = None, partition=None, basis: str = "chebyshev",
+                 tol: float = 1e-9, rank_max: int = 64):
         self.X = np.ascontiguousarray(points, dtype=np.float64)
         self.kspec = kspec
         self.leaf, self.q, self.eta = leaf, q, eta
+        if basis not in ("chebyshev", "skeleton"):
+            raise ValueError(f"unknown basis {basis!r}")
+        self.basis, self.tol, self.rank_max = basis, float(tol), int(rank_max)
         self._cache = {}
         self.tree = tree if tree is not None else ClusterTree(self.X, leaf)
         T = self.tree
@@ -311,7 +323,11 @@ class H2Matrix:
         self.diag_tree = K.diag_value(kspec.kind, self.X, kspec.weights, kspec.diag,
                                       kspec.nugget, kspec.length, kspec.degree)[T.perm]
         self._fill_near()
+        self.skeletons = None
         if self.tstar is not None:
+            if basis == "skeleton":
+                from .skeleton import Skeletons
+                self.skeletons = Skeletons(T, far, self.tstar, kspec, self.sqrt_w_tree, tol, rank_max)
             self._bases()
             self._couplings()
 
@@ -345,9 +361,13 @@ class H2Matrix:
         self.R = {}        # (ell, j) -> (r_j x k)
         self.rank = {}     # (ell, j) -> r_j
         Xt, sw = T.points_tree, self.sqrt_w_tree
+        Sk = self.skeletons
         for j in range(1 << L):
             rj = T.rows(L, j)
-            Uc = sw[rj][:, None] * C.lagrange(L, j, Xt[rj])
+            if Sk is None:
+                Uc = sw[rj][:, None] * C.lagrange(L, j, Xt[rj])
+            else:
+                Uc = Sk.leaf_basis(j)        # the weights are inside the sampled rows
             Q, R = qr_nonneg(Uc)
             self.U[j] = Q
             self.R[(L, j)] = R
@@ -356,7 +376,10 @@ class H2Matrix:
             for p in range(1 << ell):
                 blocks = []
                 for c in (2 * p, 2 * p + 1):
-                    E = C.lagrange(ell, p, C.nodes(ell + 1, c))   # E_c[a, b] = L^P_b(xi^c_a)
+                    if Sk is None:
+                        E = C.lagrange(ell, p, C.nodes(ell + 1, c))   # E_c[a, b] = L^P_b(xi^c_a)
+                    else:
+                        E = Sk.transfer(ell + 1, c)                  # rows of T_parent for c's skeleton
                     blocks.append(self.R[(ell + 1, c)] @ E)
                 M = np.vstack(blocks)
                 Q, R = qr_nonneg(M)
@@ -366,14 +389,26 @@ class H2Matrix:
                 self.R[(ell, p)] = R
                 self.rank[(ell, p)] = Q.shape[1]
 
+    def coupling_points(self, ell: int, j: int):
+        """(points, weights) whose kernel matrix is the coupling factor S^0 of cluster j:
+        the Chebyshev nodes with unit weights, or the skeleton points with sqrt(w)."""
+        if self.skeletons is None:
+            C = self.cheb
+            return C.nodes(ell, j), np.ones(C.k)
+        idx = self.skeletons.skel[(ell, j)]
+        return self.tree.points_tree[idx], self.sqrt_w_tree[idx]
+
     def _couplings(self):
-        """S_tau,sigma = R_tau k(xi_tau, xi_sigma) R_sigma^T for every far pair."""
-        C = self.cheb
+        """S_tau,sigma = R_tau S^0_tau,sigma R_sigma^T for every far pair, with
+        S^0 = k(xi_tau, xi_sigma) on the Chebyshev nodes, or the matrix entries
+        A(skel_tau, skel_sigma) on the skeletons."""
         self.S = {}
         for ell in range(self.tstar, self.L + 1):
             lst = []
             for (t, s) in self.far[ell]:
-                Sc = self._k(C.nodes(ell, t), C.nodes(ell, s))
+                Pt, wt = self.coupling_points(ell, t)
+                Ps, ws = self.coupling_points(ell, s)
+                Sc = wt[:, None] * self._k(Pt, Ps) * ws[None, :]
                 lst.append(self.R[(ell, t)] @ Sc @ self.R[(ell, s)].T)
             self.S[ell] = lst
 
@@ -478,6 +513,31 @@ class H2Matrix:
     def dense(self) -> np.ndarray:
         """The represented matrix as a dense array (user order; small N only)."""
         return self.apply(np.eye(self.tree.n))
+
+    def expanded_basis(self, ell: int, j: int) -> np.ndarray:
+        """U_tau of cluster j at level ell expanded to its points (tree order):
+        the leaf basis for ell = L, else blockdiag(children's bases) [E'_c1; E'_c2]."""
+        if ell == self.L:
+            return self.U[j]
+        B1 = self.expanded_basis(ell + 1, 2 * j)
+        B2 = self.expanded_basis(ell + 1, 2 * j + 1)
+        return np.vstack([B1 @ self.Et[(ell + 1, 2 * j)], B2 @ self.Et[(ell + 1, 2 * j + 1)]])
+
+    def dense_blocks(self) -> np.ndarray:
+        """The represented matrix assembled block by block (tree order): the close
+        blocks D and, for every far pair, U_tau S U_sigma^T with expanded bases. A
+        second route to the same matrix as ``apply`` (eq. h2 written out blockwise)."""
+        T = self.tree
+        A = np.zeros((T.n, T.n))
+        for (t, s), B in zip(self.near, self.D):
+            A[T.rows(T.L, t), T.rows(T.L, s)] = B
+        if self.tstar is None:
+            return A
+        for ell in range(self.tstar, self.L + 1):
+            Bx = {j: self.expanded_basis(ell, j) for j in range(1 << ell)}
+            for (t, s), S in zip(self.far[ell], self.S[ell]):
+                A[T.rows(ell, t), T.rows(ell, s)] = Bx[t] @ S @ Bx[s].T
+        return A
 
     def astype(self, dtype) -> "H2Matrix":
         """A shallow copy whose stored blocks are rounded to ``dtype``."""
