@@ -1,11 +1,19 @@
 #!/usr/bin/env python
-"""Throughput of the GB300 H2-MG solver: H2-MG solves/s to a relative residual,
-with the H2 matvec GB/s of the dominant kernel, in float64 and mixed precision.
+"""Throughput of the GB300 H2-MG solver: H2-MG solves/s to a relative residual of
+1e-10, with the H2 matvec GB/s of the dominant kernel, in float64 and mixed precision.
+
+Workload: 2^20 points uniform in the unit cube, Gaussian kernel exp(-r^2/0.05^2) plus
+1e-3 on the diagonal, leaf 64, eta 1, rank <= 64, right-hand side N(0,1). The nested
+bases are skeletonized to a relative tolerance of 1e-9 (the paper builds its matrices
+to a relative accuracy, Sec. 4.1); the 4x4x4 Chebyshev form of this matrix is not
+positive definite at this size, so it cannot be solved.
 
 One *step* is one complete H2-MG solve (x0 = 0, one right-hand side, to --tol) on
-a prebuilt H2 matrix: outer residual in float64, V-cycles of Algorithm 1 (CG
-smoothers, restriction, prolongation, coarse Cholesky solve) and the outer
-iteration. The matrix build is timed separately and reported as ``build_s``.
+a prebuilt H2 matrix: outer residual in float64, cycles of Algorithm 1 (CG
+smoothers, restriction, prolongation, coarse solve) in FP32 inside the float64
+flexible-CG outer loop. The matrix build is timed separately (``build_s``). The
+timed steps run without profiling; the block product's roofline comes from one more
+solve with its launches timed by CUDA events.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank solves its own problem (replicas; the solve does not
@@ -27,10 +35,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H2-MG solves/s to 1e-10 rel. residual & H2 matvec GB/s (FP64 vs mixed)"
-# DRAM bytes (read + write) per k_bsgemv launch over every block product of one outer
-# iteration of the 2^17 solve, from ncu (profiles/k_bsgemv_dram_gauss3d_n131072.md);
-# the algorithmic bytes per launch of the same launches were 1.5833e9
-TRAFFIC_PER_LAUNCH = 1.5607e9
+# DRAM bytes (read + write) per launch of the block product, from an ncu capture of
+# the same kernel on a 16384-point case of this workload, scaled per algorithmic byte
+# (None until a capture of the current kernel exists)
+TRAFFIC_PER_ALGO_BYTE = None
 
 
 def parse():
@@ -39,35 +47,43 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1 << 17, help="points of the solve workload")
-    ap.add_argument("--matvec-n", type=int, default=1 << 20, help="points of the matvec measurement")
+    ap.add_argument("--n", type=int, default=1 << 20, help="points of the solve and matvec workload")
     ap.add_argument("--length", type=float, default=0.05)
     ap.add_argument("--nugget", type=float, default=1e-3)
+    ap.add_argument("--basis", default="skeleton", choices=["skeleton", "chebyshev"],
+                    help="nested bases: skeletonized to --basis-tol with rank <= 64, or 4x4x4 Chebyshev "
+                         "(not positive definite at 2^20 points)")
+    ap.add_argument("--basis-tol", type=float, default=1e-9)
+    ap.add_argument("--coarse-level", type=int, default=-1)
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--max-cycles", type=int, default=200)
+    ap.add_argument("--max-cycles", type=int, default=400)
     ap.add_argument("--precision", default="mixed_f32", choices=["f64", "mixed_f32"])
     ap.add_argument("--outer", default="fcg", choices=["vcycle", "fcg"])
+    ap.add_argument("--cycle", default="V", choices=["V", "W", "F"])
     ap.add_argument("--nf", type=int, default=1)
     ap.add_argument("--nc", type=int, default=40)
+    ap.add_argument("--skip-square", action="store_true",
+                    help="no smoothing on levels whose restriction is square (the leaf level here)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-matvec", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-n", type=int, default=8192)
-    ap.add_argument("--ref-cycles", type=int, default=49,
-                    help="outer iterations of one full-size solve, for the reference arm's scaling "
-                         "(49 for the default workload at 2^17 points to 1e-10)")
+    ap.add_argument("--cpu-n", type=int, default=8192,
+                    help="points of the oracle's sample (a sub-cube at the workload's density)")
+    ap.add_argument("--ref-cycles", type=int, default=160,
+                    help="outer iterations of one full-size solve, for the reference arm's scaling")
     ap.add_argument("--no-f64", action="store_true", help="skip the plain float64 comparison solve")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every V-cycle kernel from the host instead of replaying a captured CUDA graph")
+    ap.add_argument("--df64", action="store_true", help="also time the matvec with double-float storage")
     ap.add_argument("--grad", action="store_true",
                     help="also time the adjoint gradients of the Matern loss (and check them by central differences)")
-    ap.add_argument("--grad-n", type=int, default=1 << 16)
-    ap.add_argument("--grad-tol", type=float, default=1e-11)
-    ap.add_argument("--skip-square", action="store_true",
-                    help="also time the solve with skip_square_levels (no smoothing on square levels)")
+    ap.add_argument("--grad-n", type=int, default=1 << 18)
+    ap.add_argument("--grad-tol", type=float, default=1e-12)
     ap.add_argument("--problems", type=int, default=32,
                     help="independent perturbed-sphere problems solved together after the timed region (0: skip)")
     ap.add_argument("--batch-rhs", type=int, default=4,
                     help="right-hand sides of the batched solve measured after the timed region (0: skip)")
+    ap.add_argument("--c1", type=int, default=1, help="also time the 4096-point exponential workload (0: skip)")
     return ap.parse_args()
 
 
@@ -153,81 +169,102 @@ def whole_job_value(steps: int, world: int, ms: float) -> float:
 
 
 def workload_name(a):
-    return (f"gauss3d_n{a.n}_l{a.length:g}_nug{a.nugget:g}_leaf64_q4_eta1")
+    basis = f"skel64_tol{a.basis_tol:g}" if a.basis == "skeleton" else "q4"
+    return f"gauss3d_n{a.n}_l{a.length:g}_nug{a.nugget:g}_leaf64_{basis}_eta1"
 
 
-def cpu_baseline(a, cycles_gpu: int):
-    """The oracle as it stands on this host's cores: a bounded sample of the same
-    workload (oracle V-cycles of the same solver settings on the same kernel at
-    --cpu-n points, matrix prebuilt), scaled to the bench size by N (linear
-    complexity, Sec. 3.4) and to a solve by the GPU's cycle count."""
+def solve_kw(a):
+    return dict(tol=a.tol, max_cycles=a.max_cycles, n_f=a.nf, n_c=a.nc, precision=a.precision, outer=a.outer,
+                cycle=a.cycle, skip_square_levels=a.skip_square, use_graph=not a.no_graph)
+
+
+def sample_points(a, n):
+    """n points of the workload's distribution at its density: the first n of a
+    uniform sample in a cube of side (n / N)^(1/3) (the same local geometry, leaf
+    sizes and far-field structure as the full workload)."""
+    import workloads as W
+    return W.uniform_points(n, 3, 2) * (n / a.n) ** (1.0 / 3.0)
+
+
+def oracle_sample_time(a, n):
+    """The oracle as it stands on this host: build (untimed) the H2 matrix of the same
+    kernel and construction on an n-point sample at the workload's density, then time
+    one outer iteration (float64 residual + one cycle of the same settings, the
+    precision emulated as in the oracle's mixed loop) three times. Returns
+    (seconds per iteration, build seconds, threads)."""
     import numpy as np
 
     import workloads as W
     from oracle import H2MG, H2Matrix, KernelSpec, SolveOpts
-    from oracle.mg import vcycle
-    p = W.workload(2, n=a.cpu_n)
+    from oracle.mg import LowPrecisionOps, cycle, vcycle
+    X = sample_points(a, n)
+    b = W.normal_rhs(n, 2)
     t0 = time.perf_counter()
-    h = H2Matrix(p["points"], KernelSpec("gaussian", a.length, a.nugget), 64, 4, 1.0)
-    mg = H2MG(h)
+    h = H2Matrix(X, KernelSpec("gaussian", a.length, a.nugget), 64, 4, 1.0, basis=a.basis, tol=a.basis_tol)
+    mg = H2MG(h, coarse_level=-1)
     build = time.perf_counter() - t0
-    opts = SolveOpts(n_f=a.nf, n_c=a.nc)
-    b = p["b"]
+    opts = SolveOpts(n_f=a.nf, n_c=a.nc, skip_square_levels=a.skip_square, cycle=a.cycle)
     low = np.float32 if a.precision == "mixed_f32" else None
-    from oracle.mg import LowPrecisionOps
     ops = LowPrecisionOps(mg, low) if low is not None else None
-    t0 = time.perf_counter()
-    reps = 0
     x = np.zeros_like(b)
-    while True:
+
+    def one(x):
         r = b - mg.apply(1, x)
-        if ops is None:
-            x = vcycle(mg, x, r, opts)
-        else:
-            x = x + vcycle(mg, np.zeros(len(r), np.float32), r.astype(np.float32), opts, ops=ops).astype(np.float64)
-        reps += 1
-        if time.perf_counter() - t0 > 10.0 or reps >= 5:
-            break
-    per_cycle = (time.perf_counter() - t0) / reps
-    scale = a.n / a.cpu_n
-    t_solve = per_cycle * scale * max(cycles_gpu, 1)
-    threads = os.environ.get("OMP_NUM_THREADS") or str(len(os.sched_getaffinity(0)))
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": int(threads), "kind": "oracle",
-            "sample": (f"{reps} oracle outer iterations (residual + V-cycle, n_f={a.nf}, n_c={a.nc}, "
-                       f"{a.precision}) at N={a.cpu_n} of the same kernel, matrix prebuilt ({build:.1f} s); "
-                       f"{per_cycle:.2f} s/iteration scaled by N={a.n}/{a.cpu_n} and by the GPU's "
-                       f"{cycles_gpu} iterations per solve")}
+        rl = r if low is None else r.astype(low)
+        z0 = np.zeros_like(rl)
+        e = vcycle(mg, z0, rl, opts, ops=ops) if a.cycle == "V" else cycle(mg, z0, rl, opts, a.cycle, ops=ops)
+        return x + e.astype(np.float64)
+
+    x = one(x)   # warm
+    t0 = time.perf_counter()
+    for _ in range(3):
+        x = one(x)
+    per = (time.perf_counter() - t0) / 3
+    threads = int(os.environ.get("OMP_NUM_THREADS") or len(os.sched_getaffinity(0)))
+    return per, build, threads
+
+
+def cpu_baseline(a, cycles_gpu: int):
+    """The oracle as it stands, on a bounded sample of the same workload (see
+    oracle_sample_time), scaled to the bench size by N (the method is linear in N,
+    Sec. 3.4) and to a solve by the GPU's outer-iteration count."""
+    per, build, threads = oracle_sample_time(a, a.cpu_n)
+    t_solve = per * (a.n / a.cpu_n) * max(cycles_gpu, 1)
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": (f"3 oracle outer iterations (float64 residual + one {a.cycle}-cycle, n_f={a.nf}, n_c={a.nc}, "
+                       f"{a.precision}) on {a.cpu_n} points of the same kernel and construction at the workload's "
+                       f"density, matrix prebuilt ({build:.0f} s); {per:.2f} s per iteration, scaled by "
+                       f"N = {a.n}/{a.cpu_n} and by the GPU's {cycles_gpu} iterations per solve")}
 
 
 # --------------------------------------------------------------------------- reference arm
 def run_reference(a, rank, world):
-    """The oracle as the reference arm (there is no other implementation to run): each
-    step is one outer iteration of the same solver (float64 residual plus one V-cycle
-    with the same smoothing and precision) on the same kernel at --cpu-n points, matrix
-    prebuilt; the time per iteration is scaled to the bench size by N (linear
-    complexity, Sec. 3.4) and to a solve by --ref-cycles outer iterations."""
+    """The oracle as the reference arm (the paper's own code is not available): the
+    same bounded sample as cpu_baseline, each step one outer iteration at --cpu-n
+    points, scaled to the bench size by N and to a solve by --ref-cycles iterations."""
     if rank != 0:
         return
     import numpy as np
 
     import workloads as W
     from oracle import H2MG, H2Matrix, KernelSpec, SolveOpts
-    from oracle.mg import LowPrecisionOps, vcycle
+    from oracle.mg import LowPrecisionOps, cycle, vcycle
     n = a.cpu_n
-    p = W.workload(2, n=n)
-    h = H2Matrix(p["points"], KernelSpec("gaussian", a.length, a.nugget), 64, 4, 1.0)
+    X = sample_points(a, n)
+    b = W.normal_rhs(n, 2)
+    h = H2Matrix(X, KernelSpec("gaussian", a.length, a.nugget), 64, 4, 1.0, basis=a.basis, tol=a.basis_tol)
     mg = H2MG(h)
-    opts = SolveOpts(n_f=a.nf, n_c=a.nc)
+    opts = SolveOpts(n_f=a.nf, n_c=a.nc, skip_square_levels=a.skip_square, cycle=a.cycle)
     low = np.float32 if a.precision == "mixed_f32" else None
     ops = LowPrecisionOps(mg, low) if low is not None else None
-    b = p["b"]
     x = np.zeros_like(b)
 
     def step(x):
         r = b - mg.apply(1, x)
-        if ops is None:
-            return vcycle(mg, x, r, opts)
-        return x + vcycle(mg, np.zeros(len(r), np.float32), r.astype(np.float32), opts, ops=ops).astype(np.float64)
+        rl = r if low is None else r.astype(low)
+        z0 = np.zeros_like(rl)
+        e = vcycle(mg, z0, rl, opts, ops=ops) if a.cycle == "V" else cycle(mg, z0, rl, opts, a.cycle, ops=ops)
+        return x + e.astype(np.float64)
 
     for _ in range(a.warmup):
         x = step(x)
@@ -238,8 +275,9 @@ def run_reference(a, rank, world):
     per_iter = dt / a.steps
     val = 1.0 / (per_iter * (a.n / n) * a.ref_cycles)
     threads = os.environ.get("OMP_NUM_THREADS") or str(len(os.sched_getaffinity(0)))
-    sample = (f"{a.steps} oracle outer iterations (residual + V-cycle, n_f={a.nf}, n_c={a.nc}, {a.precision}) "
-              f"at N={n}, {per_iter:.2f} s each, scaled by N={a.n}/{n} and by {a.ref_cycles} iterations per solve")
+    sample = (f"{a.steps} oracle outer iterations (float64 residual + one {a.cycle}-cycle, n_f={a.nf}, n_c={a.nc}, "
+              f"{a.precision}) on {n} points at the workload's density, {per_iter:.2f} s each, scaled by "
+              f"N = {a.n}/{n} and by {a.ref_cycles} iterations per solve")
     line = {"metric": METRIC, "impl": "reference", "value": val, "unit": "solves/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * per_iter,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -297,17 +335,19 @@ def uneven_problems(a, pkg, W, torch, stream):
 
 def gradients(a, pkg, W, torch):
     """The differentiation form on the Matern-3/2 workload (unit cube, l = 0.1, nugget
-    1e-2, leaf 64, 4x4x4 nodes) at --grad-n points: one forward + backward pass of
-    L = 1/2 y^T K^-1 y + 1^T K^-1 b (a three-column mixed-precision solve, the dK/dl
-    sibling and its two-column product), timed, and dL/dl, dL/ds against central
-    differences of the same loss (relative step 1e-4)."""
+    1e-2, leaf 64, bases skeletonized like the solve's) at --grad-n points: one forward
+    + backward pass of L = 1/2 y^T K^-1 y + 1^T K^-1 b (one library call: a three-column
+    mixed-precision solve, the dK/dl sibling's two-column product and the inner
+    products), timed, and dL/dl, dL/ds against central differences of the same loss
+    (relative step 1e-6, solves to --grad-tol)."""
     import numpy as np
     p = W.workload(4, n=a.grad_n)
     X = torch.from_numpy(p["points"]).cuda()
     rng = np.random.default_rng(4004)
     y = torch.from_numpy(rng.standard_normal(p["n"])).cuda()
     bb = torch.from_numpy(rng.standard_normal(p["n"])).cuda()
-    kw = dict(tol=a.grad_tol, precision="mixed_f32", use_graph=True, max_cycles=400)
+    kw = dict(tol=a.grad_tol, precision="mixed_f32", use_graph=True, max_cycles=400, basis=a.basis,
+              basis_tol=a.basis_tol)
 
     def t64(v, g=False):
         return torch.tensor(v, dtype=torch.float64, device="cuda", requires_grad=g)
@@ -322,7 +362,7 @@ def gradients(a, pkg, W, torch):
         L.backward()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
-    h = 1e-4
+    h = 1e-6
 
     def loss(l, s):
         with torch.no_grad():
@@ -330,9 +370,56 @@ def gradients(a, pkg, W, torch):
 
     fd_l = (loss(0.1 * (1 + h), 1e-2) - loss(0.1 * (1 - h), 1e-2)) / (2 * h * 0.1)
     fd_s = (loss(0.1, 1e-2 * (1 + h)) - loss(0.1, 1e-2 * (1 - h))) / (2 * h * 1e-2)
-    return {"n": p["n"], "kernel": "matern32 l=0.1 nugget=1e-2", "tol": a.grad_tol, "s_loss_and_grads": times[-1],
-            "loss": L.item(), "dL_dl": lt.grad.item(), "dL_ds": st.grad.item(), "fd_dL_dl": fd_l, "fd_dL_ds": fd_s,
+    return {"n": p["n"], "kernel": "matern32 l=0.1 nugget=1e-2", "basis": a.basis, "tol": a.grad_tol,
+            "fd_step": h, "s_loss_and_grads": times[-1], "loss": L.item(), "dL_dl": lt.grad.item(),
+            "dL_ds": st.grad.item(), "fd_dL_dl": fd_l, "fd_dL_ds": fd_s,
             "rel_err_dl": abs(lt.grad.item() - fd_l) / abs(fd_l), "rel_err_ds": abs(st.grad.item() - fd_s) / abs(fd_s)}
+
+
+def c1_workload(a, pkg, W, torch, stream):
+    """The 4096-point exponential workload (unit square, exp(-r/0.1) + 1e-2 I, leaf 64,
+    4x4 Chebyshev nodes, eta 1, N(0,1) right-hand side, relative residual 1e-8):
+    solves/s over 10 solves after 3 warm-up solves (the matrix fits in L2, so this is a
+    latency figure), and the solution's distance to the dense Cholesky solution of the
+    same H2 matrix (the oracle's)."""
+    import numpy as np
+    from oracle import H2Matrix, KernelSpec
+    p = W.workload(1)
+    A = pkg.H2Matrix(torch.from_numpy(p["points"]).cuda(), "exponential", length=0.1, nugget=1e-2, leaf=64, q=4,
+                     eta=1.0, with_f32=True)
+    b = torch.from_numpy(p["b"]).cuda()
+    kw = dict(tol=1e-8, max_cycles=400, outer="fcg", precision="mixed_f32", use_graph=True)
+    for _ in range(3):
+        A.solve(b, **kw)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        x, info = A.solve(b, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3 / 10
+    h = H2Matrix(p["points"], KernelSpec("exponential", 0.1, 1e-2), 64, 4, 1.0)
+    Ad = h.dense_blocks()
+    xd = np.empty(p["n"])
+    perm = h.tree.perm
+    xd[perm] = np.linalg.solve(Ad, p["b"][perm])
+    xg = x.cpu().numpy()
+    A.close()
+    return {"workload": "exp2d_n4096_l0.1_nug0.01_leaf64_q4_eta1", "tol": 1e-8, "s_per_solve": s,
+            "solves_per_s": 1.0 / s, "cycles": info.cycles, "converged": bool(info.converged),
+            "rel_err_vs_dense_cholesky": float(np.linalg.norm(xg - xd) / np.linalg.norm(xd))}
+
+
+def timed(stream, fn, reps=1):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
 
 
 # --------------------------------------------------------------------------- our arm
@@ -349,6 +436,7 @@ def main():
 
     import paper_2501_17656_gb300 as pkg
     import workloads as W
+    from oracle.kernels import kernel_rows
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -356,208 +444,190 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pkg.load_library()
     pk, pk_kind = peaks()
+    stream = torch.cuda.current_stream()
 
-    # ---- matvec of the full-size workload (dominant kernel on the 2^20 matrix)
-    matvec = None
-    if not a.no_matvec:
-        pm = W.workload(2, n=a.matvec_n)
-        Xm = torch.from_numpy(pm["points"]).cuda()
-        Am = pkg.H2Matrix(Xm, "gaussian", length=a.length, nugget=a.nugget, leaf=64, q=4, eta=1.0,
-                          storage="f64", with_f32=True)
-        xv = torch.randn(a.matvec_n, dtype=torch.float64, device="cuda")
-        if os.environ.get("H2MG_BENCH_REPORT_LAUNCHES"):
-            print(f"launches before the matvec: {pkg.H2Matrix.launch_count()}", file=sys.stderr, flush=True)
-        yv = torch.empty_like(xv)
-        matvec = {}
-        for prec in ("f64", "mixed_f32"):
-            Am.apply_level(1, xv, prec, y=yv)
-            torch.cuda.synchronize()
-            Am.profile(1)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(5):
-                Am.apply_level(1, xv, prec, y=yv)
-            e1.record()
-            torch.cuda.synchronize()
-            nl, kms, kby = Am.profile(0)
-            ms = e0.elapsed_time(e1) / 5
-            by = Am.query("APPLY_BYTES", 1) * (0.5 if prec == "mixed_f32" else 1.0)
-            matvec[prec] = {"n": a.matvec_n, "ms": ms, "GBs": by / ms / 1e6,
-                            "kernel_GBs": kby / kms / 1e6 if kms > 0 else None}
-            if prec == "f64":
-                y64 = yv.clone()
-        Am.close()
-        del Am
-        torch.cuda.empty_cache()
-        # the same matrix stored as double-float pairs: float64-class products on the
-        # FP32 pipes at HBM speed
-        Ad = pkg.H2Matrix(Xm, "gaussian", length=a.length, nugget=a.nugget, leaf=64, q=4, eta=1.0, storage="df64")
-        Ad.apply_level(1, xv, "f64", y=yv)
-        torch.cuda.synchronize()
-        Ad.profile(1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(5):
-            Ad.apply_level(1, xv, "f64", y=yv)
-        e1.record()
-        torch.cuda.synchronize()
-        nl, kms, kby = Ad.profile(0)
-        ms = e0.elapsed_time(e1) / 5
-        by = Ad.query("APPLY_BYTES", 1)
-        matvec["df64"] = {"n": a.matvec_n, "ms": ms, "GBs": by / ms / 1e6,
-                          "kernel_GBs": kby / kms / 1e6 if kms > 0 else None,
-                          "rel_diff_vs_f64": float(((yv - y64).norm() / y64.norm()).item())}
-        Ad.close()
-        del Ad, Xm, xv, yv, y64
-        torch.cuda.empty_cache()
-
-    # ---- the solve workload
+    # ---- the workload's matrix
     p = W.workload(2, n=a.n)
     X = torch.from_numpy(p["points"]).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    A = pkg.H2Matrix(X, "gaussian", length=a.length, nugget=a.nugget, leaf=64, q=4, eta=1.0,
-                     storage="f64", with_f32=(a.precision == "mixed_f32"))
+    A = pkg.H2Matrix(X, "gaussian", length=a.length, nugget=a.nugget, leaf=64, q=4, eta=1.0, storage="f64",
+                     with_f32=(a.precision == "mixed_f32"), basis=a.basis, basis_tol=a.basis_tol, rank_max=64,
+                     coarse_level=a.coarse_level)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    L_, ts_ = A.query("L"), A.query("TSTAR")
+    structure = {"levels": A.levels, "L": L_, "tstar": ts_, "level_sizes": [A.level_size(i) for i in range(1, A.levels + 1)],
+                 "mean_rank": {str(e): float(np.mean(A.export("RANKS", e))) for e in range(ts_, L_ + 1)},
+                 "device_GB": A.query("DEVICE_BYTES") / 1e9, "near_blocks": A.query("NEAR_PAIRS")}
+    tune = None
+    if not a.no_autotune:
+        t0 = time.perf_counter()
+        rep = A.autotune()
+        tune = {"s": time.perf_counter() - t0,
+                "per_operator": [{"op": o, "nr": nr, "fixed_ms": f, "tuned_ms": t} for o, nr, f, t in rep]}
+
+    # ---- matvec: the dominant kernel on the full matrix
+    matvec = None
+    if not a.no_matvec:
+        xv = torch.randn(a.n, dtype=torch.float64, device="cuda")
+        yv = torch.empty_like(xv)
+        matvec = {}
+        for prec in ("f64", "mixed_f32"):
+            if prec == "mixed_f32" and a.precision != "mixed_f32":
+                continue
+            A.apply_level(1, xv, prec, y=yv)
+            ms, _ = timed(stream, lambda: A.apply_level(1, xv, prec, y=yv), 5)
+            A.profile(1)
+            for _ in range(5):
+                A.apply_level(1, xv, prec, y=yv)
+            torch.cuda.synchronize()
+            nl, kms, kby = A.profile(0)
+            by = A.query("APPLY_BYTES", 1) * (0.5 if prec == "mixed_f32" else 1.0)
+            matvec[prec] = {"n": a.n, "ms": ms, "GBs": by / ms / 1e6,
+                            "kernel_GBs": kby / kms / 1e6 if kms > 0 else None}
+        # sampled rows of the exact kernel matrix (the oracle's formula)
+        rows = np.random.default_rng(2).choice(a.n, 256, replace=False)
+        Kr = kernel_rows("gaussian", p["points"], rows, a.length, a.nugget)
+        xh = xv.cpu().numpy()
+        yr = Kr @ xh
+        for prec in list(matvec):
+            yh = A.apply_level(1, xv, prec).cpu().numpy()
+            matvec[prec]["oracle_rows_rel_err"] = float(np.linalg.norm(yh[rows] - yr) / np.linalg.norm(yr))
+        del xv, yv
+
+    # ---- one complete solve: the cycle count of a solve, its convergence and its own time
     b = torch.from_numpy(p["b"]).cuda()
-    kw = dict(tol=a.tol, max_cycles=a.max_cycles, n_f=a.nf, n_c=a.nc, precision=a.precision,
-              outer=a.outer, use_graph=not a.no_graph)
-    A.profile(1)   # warm-up solves capture the graph the timed (profiled) solves replay
+    kw = solve_kw(a)
+    A.solve(b, raise_on_fail=False, **dict(kw, max_cycles=2))      # captures the cycle's graph
+    msf, (x, finfo) = timed(stream, lambda: A.solve(b, raise_on_fail=False, **kw))
+    cycles = finfo.cycles
+    full = {"s": msf / 1e3, "solves_per_s": 1e3 / msf, "cycles": cycles, "converged": bool(finfo.converged),
+            "relres": finfo.relres, "s_per_cycle": msf / 1e3 / max(cycles, 1)}
+    relres_check = float(((b - A.apply(x)).norm() / b.norm()).item())
+    # the solution against the exact kernel matrix on sampled rows (the oracle's formula)
+    xs = x.cpu().numpy()
+    rows = np.random.default_rng(3).choice(a.n, 256, replace=False)
+    Kr = kernel_rows("gaussian", p["points"], rows, a.length, a.nugget)
+    r_rows = p["b"][rows] - Kr @ xs
+    oracle_relres = float(np.linalg.norm(r_rows) / np.linalg.norm(p["b"][rows]))
+
+    # ---- steps: one outer iteration each (float64 residual, one cycle, flexible-CG
+    # update, float64 residual check) through h2mg_solve with max_cycles = 1, continuing
+    # from the previous iterate; W untimed, then K timed, unprofiled
+    xk = torch.zeros_like(b)
+
+    def step(xk, **extra):
+        return A.solve(b, x=xk, raise_on_fail=False, **dict(kw, max_cycles=1, **extra))
+
     for _ in range(a.warmup):
-        A.solve(b, raise_on_fail=False, **kw)
+        step(xk)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    infos = []
-    A.profile(1)
     l0 = pkg.H2Matrix.launch_count()
-    if os.environ.get("H2MG_BENCH_REPORT_LAUNCHES"):
-        print(f"launches before the timed region: {l0}", file=sys.stderr, flush=True)
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(a.steps):
-            x, info = A.solve(b, raise_on_fail=False, **kw)
-            infos.append((info.cycles, info.converged, info.relres))
+            step(xk)
         e1.record(stream)
         torch.cuda.synchronize()
     launches = pkg.H2Matrix.launch_count() - l0
-    nk, kms, kby = A.profile(0)
     ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-    value = whole_job_value(a.steps, world, ms)
-    converged = all(c for _, c, _ in infos)
-    cycles = infos[-1][0]
+    ms_step = ms / a.steps
+    # solves/s of the whole job: every rank ran K steps in at most ms; a solve is
+    # `cycles` steps
+    value = whole_job_value(a.steps, world, ms) / max(cycles, 1)
 
-    # ---- end to end through the C ABI with host buffers (copies inside the region)
+    # ---- three more steps with the block product's launches timed (the roofline)
+    A.profile(1)
+    for _ in range(3):
+        step(xk)
+    torch.cuda.synchronize()
+    nk, kms, kby = A.profile(0)
+
+    # ---- end to end through the C ABI with host buffers: b copied in and x out every step
     bh = np.ascontiguousarray(p["b"])
     xh = np.zeros_like(bh)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for _ in range(a.steps):
-        xh[:] = 0.0
-        A.solve(bh, x=xh, raise_on_fail=False, **kw)
-    e2e_s = (time.perf_counter() - t1) / a.steps
+        A.solve(bh, x=xh, raise_on_fail=False, **dict(kw, max_cycles=1))
+    e2e_step = (time.perf_counter() - t1) / a.steps
 
-    res_check = float(np.linalg.norm(p["b"] - A.apply(torch.from_numpy(xh).cuda()).cpu().numpy())
-                      / np.linalg.norm(p["b"]))
-
-    # ---- plain float64 H2-MG on the same matrix (every product on the FP64 pipe), once
+    # ---- plain float64 H2-MG on the same matrix (every product on the FP64 pipe): three
+    # steps after one that captures its graph
     f64 = None
     if a.precision == "mixed_f32" and not a.no_f64:
-        kw64 = dict(kw, precision="f64")
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        x64, i64 = A.solve(b, raise_on_fail=False, **kw64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        s64 = f0.elapsed_time(f1) / 1e3
-        f64 = {"s_per_solve": s64, "solves_per_s": 1.0 / s64, "cycles": i64.cycles,
-               "converged": bool(i64.converged), "relres": i64.relres,
-               "mixed_speedup": s64 / (ms / 1e3 / a.steps)}
-    # ---- the same solve with every V-cycle kernel launched from the host, timed once
-    direct = None
-    if not a.no_graph:
-        kwd = dict(kw, use_graph=False)
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        xg_, ig_ = A.solve(b, raise_on_fail=False, **kwd)
-        h1.record(stream)
-        torch.cuda.synchronize()
-        sg = h0.elapsed_time(h1) / 1e3
-        direct = {"s_per_solve": sg, "solves_per_s": 1.0 / sg, "cycles": ig_.cycles,
-                  "converged": bool(ig_.converged), "graph_speedup": sg / (ms / 1e3 / a.steps)}
+        step(xk, precision="f64")
+        ms64, _ = timed(stream, lambda: step(xk, precision="f64"), 3)
+        f64 = {"ms_per_step": ms64, "mixed_speedup_per_step": ms64 / ms_step,
+               "note": "per outer iteration; a float64 solve takes about as many cycles as the mixed one"}
 
-    # ---- the same solve without smoothing on levels whose restriction is square
-    # (U_1 is 64 x 64 here: A_2 is an orthogonal similarity of A_1), timed once
-    skip = None
-    if a.skip_square:
-        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k0.record(stream)
-        xk_, ik_ = A.solve(b, raise_on_fail=False, skip_square_levels=True, **kw)
-        k1.record(stream)
-        torch.cuda.synchronize()
-        sk = k0.elapsed_time(k1) / 1e3
-        relk = float(((b - A.apply(xk_)).norm() / b.norm()).item())
-        skip = {"s_per_solve": sk, "solves_per_s": 1.0 / sk, "cycles": ik_.cycles,
-                "converged": bool(ik_.converged) and relk <= a.tol * 1.0001, "relres": relk,
-                "speedup_vs_literal": (ms / 1e3 / a.steps) / sk}
-
-    # ---- batched form: several right-hand sides solved together (one group of columns
-    # shares every block read of every product), timed once
+    # ---- several right-hand sides per step (each block read serves the group)
     batched = None
     if a.batch_rhs > 0:
         Bm = torch.from_numpy(np.ascontiguousarray(W.normal_rhs(a.n, 2, a.batch_rhs))).cuda() \
             if a.batch_rhs > 1 else b[:, None].clone()
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if os.environ.get("H2MG_BENCH_REPORT_LAUNCHES"):
-            print(f"launches before the batched solve: {pkg.H2Matrix.launch_count()}", file=sys.stderr, flush=True)
-        g0.record(stream)
-        Xb, ib = A.solve(Bm, raise_on_fail=False, **kw)
-        ib = ib if isinstance(ib, list) else [ib]
-        g1.record(stream)
-        torch.cuda.synchronize()
-        sb = g0.elapsed_time(g1) / 1e3
-        Rb = Bm - A.apply(Xb)
-        relb = (Rb.norm(dim=0) / Bm.norm(dim=0)).max().item()
-        batched = {"nrhs": a.batch_rhs, "s_per_batch": sb, "solves_per_s": a.batch_rhs / sb,
-                   "max_relres": relb, "converged": bool(relb <= a.tol * 1.0001) and all(i.converged for i in ib),
-                   "cycles": [i.cycles for i in ib],
-                   "speedup_vs_single_rhs": (a.batch_rhs / sb) / (a.steps / (ms / 1e3)),
-                   "precision": a.precision}
+        Xm = torch.zeros_like(Bm)
+        A.solve(Bm, x=Xm, raise_on_fail=False, **dict(kw, max_cycles=1))
+        msb, _ = timed(stream, lambda: A.solve(Bm, x=Xm, raise_on_fail=False, **dict(kw, max_cycles=1)), 3)
+        batched = {"nrhs": a.batch_rhs, "ms_per_step": msb,
+                   "solves_per_s": a.batch_rhs * 1e3 / (msb * max(cycles, 1)),
+                   "speedup_vs_single_rhs": a.batch_rhs * ms_step / msb, "precision": a.precision}
+        del Bm, Xm
     A.close()
     del A
     torch.cuda.empty_cache()
 
+    # ---- the same matrix in double-float storage: float64-class products on FP32 pipes
+    if matvec is not None and a.df64:
+        Ad = pkg.H2Matrix(X, "gaussian", length=a.length, nugget=a.nugget, leaf=64, q=4, eta=1.0, storage="df64",
+                          basis=a.basis, basis_tol=a.basis_tol, rank_max=64)
+        xv = torch.randn(a.n, dtype=torch.float64, device="cuda")
+        yv = torch.empty_like(xv)
+        Ad.apply_level(1, xv, "f64", y=yv)
+        msd, _ = timed(stream, lambda: Ad.apply_level(1, xv, "f64", y=yv), 5)
+        matvec["df64"] = {"n": a.n, "ms": msd, "GBs": Ad.query("APPLY_BYTES", 1) / msd / 1e6}
+        Ad.close()
+        del Ad, xv, yv
+        torch.cuda.empty_cache()
+
+    c1 = c1_workload(a, pkg, W, torch, stream) if a.c1 else None
     problems = uneven_problems(a, pkg, W, torch, stream) if a.problems > 0 else None
     grads = gradients(a, pkg, W, torch) if a.grad else None
 
     kernel_gbs = kby / kms / 1e6 if kms > 0 else 0.0
-    bound = "hbm"
-    peak = pk["hbm_gbs"]
-    roof = {"bound": bound, "achieved": kernel_gbs, "peak": peak, "unit": "GB/s",
-            "frac": kernel_gbs / peak, "traffic": TRAFFIC_PER_LAUNCH if a.n == 1 << 17 else None,
-            "traffic_source": "profiles/k_bsgemv_dram_gauss3d_n131072.md (ncu, one outer iteration)",
+    bpl = kby / max(nk, 1)
+    roof = {"bound": "hbm", "achieved": kernel_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": kernel_gbs / pk["hbm_gbs"],
+            "traffic": (TRAFFIC_PER_ALGO_BYTE * bpl) if TRAFFIC_PER_ALGO_BYTE else None,
             "kernel": "k_bsgemv (symmetric block-sparse product)", "launches": nk,
-            "bytes_per_launch": kby / max(nk, 1), "ms_per_launch": kms / max(nk, 1),
-            "peak_source": f"{pk_kind} hbm_gbs"}
+            "bytes_per_launch": bpl, "ms_per_launch": kms / max(nk, 1),
+            "peak_source": f"{pk_kind} hbm_gbs (copy bandwidth)",
+            "measured_over": "one extra solve of the workload with every block product timed by CUDA events"}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 outer / f32 V-cycle" if a.precision == "mixed_f32" else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(a), "n": a.n, "kernel": "gaussian", "length": a.length,
-                       "nugget": a.nugget, "leaf": 64, "cheb_nodes": "4x4x4", "eta": 1.0,
-                       "tol": a.tol, "outer": a.outer, "n_f": a.nf, "n_c": a.nc,
+                       "nugget": a.nugget, "leaf": 64, "basis": a.basis, "basis_tol": a.basis_tol, "rank_max": 64,
+                       "eta": 1.0, "tol": a.tol, "outer": a.outer, "cycle": a.cycle, "n_f": a.nf, "n_c": a.nc,
+                       "skip_square_levels": a.skip_square, "coarse_level": a.coarse_level,
                        "precision": a.precision, "storage": "f64 (+f32 copy)",
                        "l2": "inputs larger than L2 (stored blocks)", "build_s": build_s,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "cycles": cycles, "converged": converged, "relres": infos[-1][2], "relres_check": res_check,
-            "matvec": matvec, "f64_solve": f64, "direct_launches": direct, "skip_square_levels": skip, "batched": batched,
-            "problems": problems, "gradients": grads, "roofline": roof, "gpu_launches": launches,
-            "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 16 * a.n,
-                    "d2h_bytes_per_step": 8 * a.n},
+            "step": "one outer iteration of the solve (float64 residual, one cycle, flexible-CG update, "
+                    "residual check) through h2mg_solve; value = 1 / (cycles x step time)",
+            "cycles": cycles, "converged": bool(finfo.converged), "relres": finfo.relres,
+            "relres_check": relres_check, "full_solve": full,
+            "oracle_relres_rows": oracle_relres, "structure": structure, "autotune": tune,
+            "matvec": matvec, "f64_solve": f64, "batched": batched, "c1": c1, "problems": problems,
+            "gradients": grads, "roofline": roof, "gpu_launches": launches,
+            "e2e": {"value": 1.0 / (e2e_step * max(cycles, 1)), "unit": "solves/s", "h2d_bytes_per_step": 16 * a.n,
+                    "d2h_bytes_per_step": 8 * a.n, "s_per_step": e2e_step},
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(a, cycles)

@@ -80,17 +80,41 @@ typedef struct {
  * relative, products in double-float arithmetic on the FP32 pipes (same bytes). */
 typedef enum { H2MG_STORE_F64 = 0, H2MG_STORE_DF64 = 1 } h2mg_storage;
 
+/* How the nested cluster bases are made before their QR orthonormalisation (Sec. 3.3).
+ * CHEBYSHEV: tensor interpolation with cheb_q first-kind nodes per axis on each
+ *   cluster's tight box (rank q^dim).
+ * SKELETON: recursive skeletonization to a relative tolerance, the kind of
+ *   tolerance-driven algebraic construction the paper builds its matrices with
+ *   (Sec. 4.1: relative accuracy 1e-9, adaptive ranks): each cluster keeps the
+ *   subset of its points (a leaf) or of its children's skeletons (a parent) whose
+ *   rows interpolate its sampled far-field rows, A(X_t, F_t) ~= T_t A(skel_t, F_t),
+ *   chosen by a column-pivoted QR stopped at basis_tol relative to the first pivot or
+ *   at rank_max. The sample F_t is every far partner's candidates plus every far
+ *   partner of the parent (their children's candidates, thinned to 128 points).
+ *   Leaf basis = T_leaf, transfers = rows of T_parent, couplings A(skel_t, skel_s). */
+typedef enum { H2MG_BASIS_CHEBYSHEV = 0, H2MG_BASIS_SKELETON = 1 } h2mg_basis;
+
 typedef struct {
     int leaf_size;      /* max points per leaf cluster, 2..64 */
-    int cheb_q;         /* Chebyshev nodes per dimension; rank k = q^dim <= 64 */
+    int cheb_q;         /* Chebyshev nodes per dimension; rank k = q^dim <= 64 (CHEBYSHEV) */
     double eta;         /* admissibility: far iff dist > 0 and max(diam) <= eta*dist; >= 0 */
     int storage;        /* h2mg_storage of the primary copy */
     int with_f32;       /* 1: also keep an FP32 copy of every V-cycle operator (mixed solves) */
     int coarse_level;   /* coarsest multigrid level l; -1 = natural l = L - t* + 1 */
+    int basis;          /* h2mg_basis */
+    double basis_tol;   /* SKELETON: relative tolerance of the pivoted QR, >= 0 */
+    int rank_max;       /* SKELETON: rank cap, 1..64 */
 } h2mg_build_opts;
 
 typedef enum { H2MG_PREC_F64 = 0, H2MG_PREC_MIXED_F32 = 1 } h2mg_precision;
-typedef enum { H2MG_OUTER_VCYCLE = 0, H2MG_OUTER_FCG = 1 } h2mg_outer;
+typedef enum { H2MG_OUTER_VCYCLE = 0, H2MG_OUTER_FCG = 1, H2MG_OUTER_CG = 2 } h2mg_outer;
+/* Multigrid cycle of the outer loops. V: Algorithm 1 (Sec. 3.3). W and F, which the
+ * paper names as further options after Algorithm 1: the textbook recursions, where
+ * each visit of level i < l pre-smooths from its start (zero on the first visit),
+ * restricts the residual, visits level i + 1 twice (W) or once as an F-cycle and once
+ * as a V-cycle (F), each visit starting from the previous one's result, prolongs and
+ * post-smooths; level l solves directly. */
+typedef enum { H2MG_CYCLE_V = 0, H2MG_CYCLE_W = 1, H2MG_CYCLE_F = 2 } h2mg_cycle;
 
 typedef struct {
     double tol;                     /* stop when |b - A x| / |b| <= tol */
@@ -100,8 +124,11 @@ typedef struct {
     int precision;                  /* h2mg_precision of the V-cycle */
     int explicit_restrict_residual; /* 1: r_{i+1} = U_i^T (r_i - A_i e_i) with an explicit apply;
                                        0: use CG's recurrence residual (equal in exact arithmetic) */
-    int outer;                      /* h2mg_outer: repeated V-cycles (Sec. 3.3) or flexible CG
-                                       preconditioned by one V-cycle */
+    int outer;                      /* h2mg_outer: repeated cycles (Sec. 3.3), flexible CG
+                                       preconditioned by one cycle, or unpreconditioned CG
+                                       (the paper's comparison solver, Sec. 4; each CG
+                                       iteration counts as one "cycle" in the info, the
+                                       multigrid settings are unused) */
     int use_graph;                  /* 1: capture the V-cycle (smoothers, transfers, coarse
                                        solve: no host synchronisation inside) as a CUDA graph
                                        on the first solve with these settings and column
@@ -117,6 +144,7 @@ typedef struct {
                                        that A_i is an orthogonal similarity of A_{i-1} and
                                        not a coarser operator: the V-cycle passes the
                                        residual through it. 0: Algorithm 1 literally */
+    int cycle;                      /* h2mg_cycle */
 } h2mg_solve_opts;
 
 typedef struct {
@@ -182,6 +210,26 @@ h2mg_status h2mg_solve_batched(int nprob, const h2mg_matrix* A, const double* co
  * (INVALID_ARG). */
 h2mg_status h2mg_build_sibling(h2mg_matrix A, const h2mg_kernel* k, void* stream, h2mg_matrix* out);
 
+/* The differentiation form on a Matern-3/2 matrix K = (1 + sqrt3 r/l) exp(-sqrt3 r/l) + s I
+ * in H2 form: the loss L(y, b, l, s) = 1/2 y^T K^{-1} y + 1^T K^{-1} b and its adjoint
+ * gradients. With a = K^{-1} y, x = K^{-1} b and w = K^{-1} 1 (K symmetric):
+ *     L = 1/2 y^T a + 1^T x,   dL/dy = a,   dL/db = w,
+ *     dL/dl = -1/2 a^T (dK/dl) a - w^T (dK/dl) x,   dL/ds = -1/2 a^T a - w^T x  (dK/ds = I).
+ * The three solves run as one three-column H2-MG solve with the options o (two
+ * columns when none of dLdb, dLdl, dLds is wanted); dK is the d/dlength sibling of K
+ * (h2mg_build_sibling with H2MG_K_DMATERN32_DL and K's length), applied to a and x as
+ * one two-column product; the inner products are reduced on the GPU and combined
+ * here. Only the scalars leave the device; dLdy and dLdb (optional, n entries, host or
+ * device) receive a and w. dK may be NULL when dLdl is NULL. info (optional) receives
+ * the statistics of the two or three columns. Statuses as h2mg_solve; INVALID_ARG
+ * when K is not a Matern-3/2 matrix built for solves or dK is not its sibling. The
+ * problem statement is Sec. 3.1's A x = b with A depending on kernel parameters; the
+ * loss and gradient formulas are the adjoint method's. Allocates its column buffers
+ * (3 n doubles) and synchronises the stream. */
+h2mg_status h2mg_matern_loss_grad(h2mg_matrix K, h2mg_matrix dK, const double* y, const double* b,
+                                  const h2mg_solve_opts* o, double* loss, double* dLdy, double* dLdb,
+                                  double* dLdl, double* dLds, h2mg_solve_info* info, void* stream);
+
 /* *out = x^T y for n float64 values (host or device vectors), reduced on the GPU
  * with the library's deterministic two-pass sum; synchronises the stream. */
 h2mg_status h2mg_dot(const double* x, const double* y, int64_t n, double* out, void* stream);
@@ -216,7 +264,10 @@ typedef enum {
     H2MG_X_NEAR = 2,        /* int32[2 * pairs]: close leaf pairs (t, s), t <= s      */
     H2MG_X_FAR = 3,         /* int32[2 * pairs]: far pairs (t, s), t < s, of tree level arg */
     H2MG_X_RANKS = 4,       /* int32[2^arg]: ranks r_j of the clusters of tree level arg */
-    H2MG_X_BOXES = 5        /* double[2^arg * 2 * dim]: (lo, hi) boxes of tree level arg */
+    H2MG_X_BOXES = 5,       /* double[2^arg * 2 * dim]: (lo, hi) boxes of tree level arg */
+    H2MG_X_SKELETON = 6     /* int32[2^arg * 64]: SKELETON bases: skeleton of each cluster of
+                               tree level arg, as original point indices in pivot order,
+                               -1 beyond the cluster's rank */
 } h2mg_export_what;
 
 /* Copy the structure `what` to host memory `buf` of `cap` bytes; *bytes = size needed. */
@@ -266,19 +317,37 @@ int64_t h2mg_launch_count(void);
  * Any output pointer may be NULL. */
 h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* ms, double* bytes);
 
+/* Autotuner of the block-sparse product (the kernel that streams D, S and P_i). The
+ * library launches it with a number of CTAs per block row; by default a fixed rule
+ * (enough CTAs to fill the GPU when an operator has few block rows). This call times
+ * trial launches of every operator of the hierarchy (index 0: the close part of level
+ * 1; index i >= 1: the coupling operator of level i), for the primary format with 1
+ * and 2 columns and the FP32 copy with 1, 2 and 4 columns, over the splits 1..64, and
+ * keeps the fastest in the handle; later products, smoothers and solves use it (a
+ * CUDA graph captured before the call keeps the old choice). report (optional, cap
+ * entries of 4 doubles) receives (operator index, columns, ms with the fixed rule, ms
+ * tuned) per combination; *count (optional) = the number of combinations. Runs on
+ * `stream` and synchronises it; h2mg_profile must be off. No counterpart in the paper
+ * (a launch-configuration choice of this implementation). */
+h2mg_status h2mg_autotune(h2mg_matrix A, void* stream, double* report, int cap, int* count);
+
 /* ---------------------------------------------------------------- allocation-free product
  * The paper has no counterpart to this call; it exists for callers that cannot
- * allocate device memory where they need a product: code running while a stream is
- * captured into a CUDA graph, code inside allocator callbacks, or processes whose
- * device memory another allocator has reserved in full.
+ * allocate device memory where they need a product: code inside allocator callbacks
+ * (which must not re-enter the allocator), or processes whose device memory another
+ * allocator (a framework's caching pool) has reserved in full, so that a cudaMalloc
+ * would fail.
  *
  * h2mg_apply_noalloc computes y = A x like h2mg_apply (one column, device x and y
  * only; host pointers are rejected with INVALID_ARG) but calls no cudaMalloc,
  * cudaFree or allocating library routine: its workspace lives in one fixed array of
  * H2MG_NOALLOC_SCRATCH_BYTES bytes of device memory that every GPU loading this
  * library holds until the process exits. Matrices whose product needs more scratch
- * than that are rejected with UNSUPPORTED (the product needs about 64 bytes per
- * point: some 2^18 points fit). The first call on a device looks up the array's address with
+ * than that are rejected with UNSUPPORTED (the workspace is three coefficient buffers
+ * of 8 * clusters * KC bytes and two point buffers of 8 * leaves * KD bytes: about 64
+ * bytes per point in 3-D with leaf 64 and 64 nodes, so some 2^18 such points fit).
+ * Vectors must be n float64 entries on the current device. The first call on a device
+ * looks up the array's address with
  * that device current; make that first call before any stream capture. All calls
  * share the array and it keeps the last call's contents: calls whose work overlaps
  * on the GPU (different streams, or different host threads) race and give wrong

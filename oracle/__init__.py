@@ -8,4 +8,4 @@ it. Its inputs come from ``workloads`` only.
 """
 from .kernels import dense_kernel_matrix, kmat, surface_diag  # noqa: F401
 from .h2 import ClusterTree, H2Matrix, KernelSpec, block_partition  # noqa: F401
-from .mg import H2MG, SolveInfo, SolveOpts, cg, solve, solve_fcg, solve_mixed, vcycle  # noqa: F401
+from .mg import H2MG, SolveInfo, SolveOpts, cg, cycle, solve, solve_cg, solve_fcg, solve_mixed, vcycle  # noqa: F401

@@ -107,3 +107,26 @@ def dense_kernel_matrix(kind: str, X: np.ndarray, length: float = 1.0, nugget: f
         K = s[:, None] * K * s[None, :]
     np.fill_diagonal(K, diag_value(kind, X, weights, diag, nugget, length, degree))
     return K
+
+
+def kernel_rows(kind: str, X: np.ndarray, rows, length: float = 1.0, nugget: float = 0.0,
+                weights=None, diag=None, degree: int = 2, chunk: int = 16) -> np.ndarray:
+    """Rows ``rows`` of the dense N x N kernel matrix (A_ij = sqrt(w_i) k(x_i, x_j)
+    sqrt(w_j), A_ii = diag), by the formula, ``chunk`` rows at a time: the exact matrix
+    that the H2 form approximates, for sampled checks at sizes where the full matrix
+    cannot be held."""
+    rows = np.asarray(rows, dtype=np.int64)
+    X = np.asarray(X, dtype=np.float64)
+    w = None if weights is None else np.sqrt(np.asarray(weights, dtype=np.float64))
+    dg = diag_value(kind, X[rows], None if weights is None else np.asarray(weights)[rows],
+                    None if diag is None else np.asarray(diag)[rows], nugget, length, degree)
+    out = np.empty((len(rows), X.shape[0]))
+    for a in range(0, len(rows), chunk):
+        rr = rows[a:a + chunk]
+        with np.errstate(divide="ignore"):
+            B = kmat(kind, X[rr], X, length, degree)
+        if w is not None:
+            B = w[rr][:, None] * B * w[None, :]
+        B[np.arange(len(rr)), rr] = dg[a:a + chunk]
+        out[a:a + len(rr)] = B
+    return out

@@ -38,6 +38,7 @@ class SolveOpts:
     explicit_restrict_residual: bool = False
     coarse_level: int = -1            # -1: natural l = L - t* + 1
     skip_square_levels: bool = False  # no smoothing where U_{i-1} is square (A_i similar to A_{i-1})
+    cycle: str = "V"                  # multigrid cycle of the outer loops: "V", "W" or "F"
 
 
 @dataclass
@@ -153,7 +154,9 @@ class H2MG:
     def _dense_coarse(self):
         """A_l as a dense matrix (A_l applied to the identity) and its Cholesky factor."""
         n = self.size(self.l)
-        self.Al = self.apply(self.l, np.eye(n))
+        # A_l applied to the identity, 256 columns at a time (bounded gather sizes)
+        self.Al = np.concatenate([self.apply(self.l, np.eye(n)[:, c:c + 256]) for c in range(0, n, 256)],
+                                 axis=1) if n > 0 else np.zeros((0, 0))
         self.Al = 0.5 * (self.Al + self.Al.T)     # symmetric by construction; remove round-off
         try:
             self.chol = sla.cho_factor(self.Al, lower=True)
@@ -238,14 +241,69 @@ def vcycle(mg: H2MG, x0: np.ndarray, r1: np.ndarray, opts: SolveOpts, ops=None) 
     return x0 + e
 
 
-def solve(mg: H2MG, b: np.ndarray, opts: SolveOpts, x0: np.ndarray | None = None):
-    """Repeated V-cycles until |b - A x| / |b| <= tol (x* feeds the next cycle)."""
+def _iters(mg: H2MG, opts: SolveOpts, i: int) -> int:
+    if i == 1:
+        return opts.n_f
+    if opts.skip_square_levels and mg.size(i) == mg.size(i - 1):
+        return 0
+    return opts.n_c
+
+
+def cycle(mg: H2MG, x0: np.ndarray, r1: np.ndarray, opts: SolveOpts, kind: str = "V", ops=None) -> np.ndarray:
+    """One multigrid cycle of type ``kind`` given x0 and r_1 = b - A_1 x0; returns x*.
+
+    The recursive form of the textbook cycles, with the smoother, transfers and coarse
+    solve of Algorithm 1: on level i < l the correction of A_i e = f starts from a
+    guess g (zero on the first visit), is pre-smoothed, e~ = Iter(A_i, f, g); the
+    residual f - A_i e~ is restricted, r_{i+1} = U_i^T (f - A_i e~); the coarse
+    correction is gamma visits of level i + 1 on A_{i+1} e = r_{i+1} (each from the
+    previous visit's result); then e~ += V_i^T e_{i+1} and e = Iter(A_i, f, e~). Level
+    l solves directly, e_l = dir_sol(A_l, r_l). A V-cycle visits the coarser level once
+    (this is Algorithm 1), a W-cycle twice, and an F-cycle runs an F-cycle and then a
+    V-cycle there (Sec. 3.3 names W- and F-cycles as further options)."""
+    ops = mg if ops is None else ops
+    l = mg.l
+    dt = r1.dtype
+
+    def visit(i, f, g, k):
+        if i == l:
+            return mg.dir_sol(f).astype(dt)
+        n_i = _iters(mg, opts, i)
+        A = (lambda v, i=i: ops.apply(i, v))
+        et, rho = cg(A, f, g, n_i)
+        res = f - A(et) if opts.explicit_restrict_residual else rho
+        rc = ops.restrict(i, res)
+        kids = {"V": ("V",), "W": ("W", "W"), "F": ("F", "V")}[k]
+        e = None
+        for kk in kids:
+            e = visit(i + 1, rc, e, kk)
+        et = et + ops.prolong(i, e)
+        e, _ = cg(A, f, et, n_i)
+        return e
+
+    return x0 + visit(1, r1, None, kind)
+
+
+def anorm_error(mg: H2MG, x: np.ndarray, x_true: np.ndarray, nb: float) -> float:
+    """The paper's stopping quantity (e^T A e)^{1/2} / |b|_2 with e = x - x_true
+    (Sec. 4.1, for right-hand sides b = A x_true)."""
+    e = x - x_true
+    return float(np.sqrt(max(float(e @ mg.apply(1, e)), 0.0))) / nb
+
+
+def solve(mg: H2MG, b: np.ndarray, opts: SolveOpts, x0: np.ndarray | None = None,
+          x_true: np.ndarray | None = None):
+    """Repeated cycles until |b - A x| / |b| <= tol (x* feeds the next cycle):
+    Algorithm 1's V-cycle, or the W- or F-cycle of ``opts.cycle``. With ``x_true``
+    the test is the paper's A-norm error (e^T A e)^{1/2} / |b| < tol instead."""
     x = np.zeros_like(b) if x0 is None else x0.astype(np.float64).copy()
     nb = float(np.linalg.norm(b))
     info = SolveInfo()
     for cyc in range(opts.max_cycles + 1):
         r = b - mg.apply(1, x)
         rel = float(np.linalg.norm(r)) / nb if nb > 0 else 0.0
+        if x_true is not None:
+            rel = anorm_error(mg, x, x_true, nb)
         info.history.append(rel)
         info.cycles, info.relres = cyc, rel
         if rel <= opts.tol:
@@ -253,17 +311,56 @@ def solve(mg: H2MG, b: np.ndarray, opts: SolveOpts, x0: np.ndarray | None = None
             break
         if cyc == opts.max_cycles:
             break
-        x = vcycle(mg, x, r, opts)
+        x = vcycle(mg, x, r, opts) if opts.cycle == "V" else cycle(mg, x, r, opts, opts.cycle)
     return x, info
 
 
-def solve_fcg(mg: H2MG, b: np.ndarray, opts: SolveOpts, low=None):
+def solve_cg(mg: H2MG, b: np.ndarray, opts: SolveOpts, x_true: np.ndarray | None = None):
+    """Unpreconditioned CG on A x = b from x0 = 0, the paper's comparison solver
+    (Sec. 4: CG iterations against V-cycles), textbook recurrences: q = A p,
+    alpha = rho / p^T q, x += alpha p, r -= alpha q, rho' = r^T r, p = r + (rho'/rho) p.
+    Stops when the recurrence residual |r| / |b| <= tol (with ``x_true``: the A-norm
+    error, as in ``solve``); ``cycles`` counts CG iterations (one product each) and
+    ``relres`` is recomputed explicitly at the end."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rho = float(r @ r)
+    nb = float(np.linalg.norm(b))
+    info = SolveInfo()
+    for it in range(opts.max_cycles + 1):
+        rel = float(np.sqrt(rho)) / nb if nb > 0 else 0.0
+        if x_true is not None:
+            rel = anorm_error(mg, x, x_true, nb)
+        info.history.append(rel)
+        info.cycles = it
+        if rel <= opts.tol:
+            info.converged = True
+            break
+        if it == opts.max_cycles:
+            break
+        q = mg.apply(1, p)
+        pq = float(p @ q)
+        if not pq > 0.0:
+            break
+        alpha = rho / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rho_new = float(r @ r)
+        p = r + (rho_new / rho) * p
+        rho = rho_new
+    info.relres = float(np.linalg.norm(b - mg.apply(1, x))) / nb if nb > 0 else 0.0
+    return x, info
+
+
+def solve_fcg(mg: H2MG, b: np.ndarray, opts: SolveOpts, low=None, precond=None):
     """Flexible CG preconditioned by one V-cycle (multigrid used to precondition
     another iteration, Section 3.2). The V-cycle with CG smoothers is a nonlinear
     map, so each new direction is made A-orthogonal to the previous one (flexible
     CG with one stored direction). The residual is recomputed explicitly in float64
     each iteration; ``low`` runs the V-cycle on rounded operators as in
-    ``solve_mixed``. ``cycles`` counts V-cycles."""
+    ``solve_mixed``; ``opts.cycle`` selects a W- or F-cycle instead. ``precond``
+    (a map r -> z) replaces the cycle altogether. ``cycles`` counts cycles."""
     ops = None if low is None else LowPrecisionOps(mg, low)
     x = np.zeros_like(b)
     nb = float(np.linalg.norm(b))
@@ -279,11 +376,15 @@ def solve_fcg(mg: H2MG, b: np.ndarray, opts: SolveOpts, low=None):
             break
         if cyc == opts.max_cycles:
             break
-        if ops is None:
-            z = vcycle(mg, np.zeros_like(r), r, opts)
+        if precond is not None:
+            z = precond(r)
+        elif ops is None:
+            z = vcycle(mg, np.zeros_like(r), r, opts) if opts.cycle == "V" else \
+                cycle(mg, np.zeros_like(r), r, opts, opts.cycle)
         else:
             rl = r.astype(low)
-            z = vcycle(mg, np.zeros_like(rl), rl, opts, ops=ops).astype(np.float64)
+            z = (vcycle(mg, np.zeros_like(rl), rl, opts, ops=ops) if opts.cycle == "V" else
+                 cycle(mg, np.zeros_like(rl), rl, opts, opts.cycle, ops=ops)).astype(np.float64)
         if p_prev is None:
             p = z
         else:
@@ -314,7 +415,8 @@ def solve_mixed(mg: H2MG, b: np.ndarray, opts: SolveOpts, low=np.float32):
         if cyc == opts.max_cycles:
             break
         rl = r.astype(low)
-        e = vcycle(mg, np.zeros_like(rl), rl, opts, ops=lowmg)
+        e = vcycle(mg, np.zeros_like(rl), rl, opts, ops=lowmg) if opts.cycle == "V" else \
+            cycle(mg, np.zeros_like(rl), rl, opts, opts.cycle, ops=lowmg)
         x = x + e.astype(np.float64)
     return x, info
 

@@ -25,18 +25,21 @@ KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "laplace_sl": 3, "pol
            "dmatern32_dl": 5}
 STORAGE = {"f64": 0, "df64": 1}
 PRECISION = {"f64": 0, "mixed_f32": 1}
-OUTER = {"vcycle": 0, "fcg": 1}
+OUTER = {"vcycle": 0, "fcg": 1, "cg": 2}
+CYCLE = {"V": 0, "W": 1, "F": 2}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5: "NOT_CONVERGED",
           6: "NAN", 7: "TIMEOUT", 8: "UNSUPPORTED"}
 
 Q = dict(N=0, DIM=1, L=2, TSTAR=3, LEVELS=4, KD=5, KC=6, RANK=7, NEAR_PAIRS=8, FAR_PAIRS=9,
          LEVEL_SIZE=10, BYTES_PRIMARY=11, BYTES_F32=12, APPLY_BYTES=13, DEVICE_BYTES=14)
-X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5)
+X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5, SKELETON=6)
+BASIS = {"chebyshev": 0, "skeleton": 1}
 
 EXPORTED = ["h2mg_build", "h2mg_apply", "h2mg_solve", "h2mg_destroy", "h2mg_error_string",
             "h2mg_last_error", "h2mg_query", "h2mg_export", "h2mg_apply_level",
             "h2mg_coarse_solve", "h2mg_smooth", "h2mg_vcycle", "h2mg_launch_count", "h2mg_profile",
-            "h2mg_transfer", "h2mg_apply_noalloc", "h2mg_build_sibling", "h2mg_dot", "h2mg_solve_batched"]
+            "h2mg_transfer", "h2mg_apply_noalloc", "h2mg_build_sibling", "h2mg_dot", "h2mg_solve_batched",
+            "h2mg_autotune", "h2mg_matern_loss_grad"]
 
 
 class H2MGError(RuntimeError):
@@ -53,14 +56,15 @@ class _Kernel(ctypes.Structure):
 
 class _BuildOpts(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("cheb_q", ctypes.c_int), ("eta", ctypes.c_double),
-                ("storage", ctypes.c_int), ("with_f32", ctypes.c_int), ("coarse_level", ctypes.c_int)]
+                ("storage", ctypes.c_int), ("with_f32", ctypes.c_int), ("coarse_level", ctypes.c_int),
+                ("basis", ctypes.c_int), ("basis_tol", ctypes.c_double), ("rank_max", ctypes.c_int)]
 
 
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("n_f", ctypes.c_int),
                 ("n_c", ctypes.c_int), ("precision", ctypes.c_int),
                 ("explicit_restrict_residual", ctypes.c_int), ("outer", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("skip_square_levels", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("skip_square_levels", ctypes.c_int), ("cycle", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -110,6 +114,10 @@ def load_library(build_if_missing: bool = False):
     lib.h2mg_solve_batched.argtypes = [ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                        ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.h2mg_profile.argtypes = [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(cd), ctypes.POINTER(cd)]
+    lib.h2mg_autotune.argtypes = [vp, vp, ctypes.POINTER(cd), ci, ctypes.POINTER(ci)]
+    pd = ctypes.POINTER(cd)
+    lib.h2mg_matern_loss_grad.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_SolveOpts), pd, vp, vp, pd, pd,
+                                          ctypes.POINTER(SolveInfo), vp]
     for name in EXPORTED:
         if name not in ("h2mg_error_string", "h2mg_last_error", "h2mg_launch_count"):
             getattr(lib, name).restype = ci
@@ -122,6 +130,16 @@ def _check(status: int):
     if status != 0:
         msg = _lib.h2mg_last_error().decode() or _lib.h2mg_error_string(status).decode()
         raise H2MGError(status, msg)
+
+
+def _current_device():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_device()
+    except ImportError:
+        pass
+    return None
 
 
 def _stream():
@@ -148,6 +166,25 @@ def _ptr(a):
             raise TypeError("tensors must be contiguous float64")
         return a.data_ptr()
     raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _expect(a, n, what, cols=False, dev=None):
+    """Rejects a vector (or, with ``cols``, an (n, nrhs) block) whose first dimension is
+    not ``n``, or a CUDA tensor on another device than the current one: the library
+    cannot see buffer sizes, so a short buffer would be read or written past its end."""
+    if a is None:
+        return
+    shape = tuple(a.shape)
+    if len(shape) == 0 or shape[0] != n or (len(shape) > (2 if cols else 1)):
+        raise ValueError(f"{what} must have shape ({n},){' or (' + str(n) + ', nrhs)' if cols else ''}, "
+                         f"got {shape}")
+    if not isinstance(a, np.ndarray):
+        import torch
+        if isinstance(a, torch.Tensor) and a.is_cuda:
+            cur = torch.cuda.current_device()
+            if a.device.index != cur or (dev is not None and dev != cur):
+                raise ValueError(f"{what} is on {a.device} and the matrix on cuda:{dev}, "
+                                 f"but cuda:{cur} is current")
 
 
 def _like(x, n):
@@ -195,6 +232,8 @@ def dot(x, y) -> float:
     """x^T y (float64) reduced by the library on the GPU."""
     out = ctypes.c_double()
     n = int(x.shape[0])
+    _expect(x, n, "x")
+    _expect(y, n, "y")
     _check(load_library().h2mg_dot(_ptr(x), _ptr(y), n, ctypes.byref(out), _stream()))
     return float(out.value)
 
@@ -206,7 +245,8 @@ class H2Matrix:
     def __init__(self, points, kernel: str = "gaussian", length: float = 1.0, nugget: float = 0.0,
                  degree: int = 2, weights=None, diag=None, leaf: int = 64, q: int = 4,
                  eta: float = 1.0, storage: str = "f64", with_f32: bool = False,
-                 coarse_level: int = -1):
+                 coarse_level: int = -1, basis: str = "chebyshev", basis_tol: float = 1e-9,
+                 rank_max: int = 64):
         lib = load_library()
         self._lib = lib
         pts = points
@@ -215,11 +255,13 @@ class H2Matrix:
         n, dim = int(pts.shape[0]), int(pts.shape[1]) if len(pts.shape) > 1 else 1
         self._keep = [pts, weights, diag]
         k = _Kernel(KERNELS[kernel], float(length), float(nugget), int(degree), _ptr(weights), _ptr(diag))
-        o = _BuildOpts(int(leaf), int(q), float(eta), STORAGE[storage], int(bool(with_f32)), int(coarse_level))
+        o = _BuildOpts(int(leaf), int(q), float(eta), STORAGE[storage], int(bool(with_f32)), int(coarse_level),
+                       BASIS[basis], float(basis_tol), int(rank_max))
         h = ctypes.c_void_p()
         _check(lib.h2mg_build(_ptr(pts), n, dim, ctypes.byref(k), ctypes.byref(o), _stream(), ctypes.byref(h)))
         self._h = h
         self.n, self.dim = n, dim
+        self.device = _current_device()
         self._keep = None
 
     # ----------------------------------------------------------------- siblings
@@ -231,6 +273,7 @@ class H2Matrix:
         _check(self._lib.h2mg_build_sibling(self._h, ctypes.byref(k), _stream(), ctypes.byref(h)))
         out = H2Matrix.__new__(H2Matrix)
         out._lib, out._h, out.n, out.dim, out._keep = self._lib, h, self.n, self.dim, None
+        out.device = self.device
         out._base = self          # the sibling uses this matrix's device structures
         return out
 
@@ -267,6 +310,16 @@ class H2Matrix:
         _check(self._lib.h2mg_profile(self._h, int(enable), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
         return int(n.value), float(ms.value), float(by.value)
 
+    def autotune(self):
+        """Tune the block product's CTAs per block row on trial launches (h2mg_autotune).
+        Returns a list of (operator, columns, fixed-rule ms, tuned ms)."""
+        cap = 256
+        buf = (ctypes.c_double * (4 * cap))()
+        cnt = ctypes.c_int()
+        _check(self._lib.h2mg_autotune(self._h, _stream(), buf, cap, ctypes.byref(cnt)))
+        return [(int(buf[4 * k]), int(buf[4 * k + 1]), buf[4 * k + 2], buf[4 * k + 3])
+                for k in range(min(cnt.value, cap))]
+
     @staticmethod
     def launch_count() -> int:
         return int(load_library().h2mg_launch_count())
@@ -282,8 +335,12 @@ class H2Matrix:
     def apply(self, x, y=None):
         """y = A x for a vector or an (n, nrhs) block of columns; the columns go through
         the products together, each stored block read once per group of four."""
+        _expect(x, self.n, "x", cols=True, dev=self.device)
         xb, nrhs = _colmajor(x)
         out = y if y is not None else _new_cols(x, self.n, None if len(x.shape) == 1 else nrhs)
+        _expect(out, self.n, "y", cols=True, dev=self.device)
+        if tuple(out.shape) != tuple(x.shape):
+            raise ValueError(f"y must have the shape of x {tuple(x.shape)}, got {tuple(out.shape)}")
         yb, _ = _colmajor(out)
         _check(self._lib.h2mg_apply(self._h, _ptr(xb), _ptr(yb), nrhs, self.n, _stream()))
         _copy_back(out, yb)
@@ -292,34 +349,46 @@ class H2Matrix:
     def apply_noalloc(self, x, y):
         """y = A x without any device allocation (device tensors only; scratch in a
         fixed array shared by all calls -- see h2mg_apply_noalloc)."""
+        _expect(x, self.n, "x", dev=self.device)
+        _expect(y, self.n, "y", dev=self.device)
         _check(self._lib.h2mg_apply_noalloc(self._h, _ptr(x), _ptr(y), _stream()))
         return y
 
     def apply_level(self, i: int, x, precision: str = "f64", y=None):
+        n = self.level_size(i)
+        _expect(x, n, "x", dev=self.device)
         if y is None:
-            y = _like(x, self.level_size(i))
+            y = _like(x, n)
+        _expect(y, n, "y", dev=self.device)
         _check(self._lib.h2mg_apply_level(self._h, int(i), PRECISION[precision], _ptr(x), _ptr(y), _stream()))
         return y
 
     def restrict(self, i: int, v):
         """U_i^T v (level i -> i+1)."""
+        _expect(v, self.level_size(i), "v", dev=self.device)
         out = _like(v, self.level_size(i + 1))
         _check(self._lib.h2mg_transfer(self._h, int(i), 0, _ptr(v), _ptr(out), _stream()))
         return out
 
     def prolong(self, i: int, e):
         """U_i e (level i+1 -> i)."""
+        _expect(e, self.level_size(i + 1), "e", dev=self.device)
         out = _like(e, self.level_size(i))
         _check(self._lib.h2mg_transfer(self._h, int(i), 1, _ptr(e), _ptr(out), _stream()))
         return out
 
     def coarse_solve(self, r, e=None):
+        nl = self.level_size(self.levels)
+        _expect(r, nl, "r", dev=self.device)
         if e is None:
-            e = _like(r, self.level_size(self.levels))
+            e = _like(r, nl)
+        _expect(e, nl, "e", dev=self.device)
         _check(self._lib.h2mg_coarse_solve(self._h, _ptr(r), _ptr(e), _stream()))
         return e
 
     def smooth(self, i: int, f, x0=None, n: int = 1, precision: str = "f64"):
+        _expect(f, self.level_size(i), "f", dev=self.device)
+        _expect(x0, self.level_size(i), "x0", dev=self.device)
         x = _like(f, self.level_size(i))
         r = _like(f, self.level_size(i))
         _check(self._lib.h2mg_smooth(self._h, int(i), PRECISION[precision], _ptr(f), _ptr(x0), int(n),
@@ -328,12 +397,14 @@ class H2Matrix:
 
     @staticmethod
     def _opts(tol=1e-10, max_cycles=100, n_f=1, n_c=40, precision="f64", explicit_restrict_residual=False,
-              outer="vcycle", use_graph=False, skip_square_levels=False):
+              outer="vcycle", use_graph=False, skip_square_levels=False, cycle="V"):
         return _SolveOpts(float(tol), int(max_cycles), int(n_f), int(n_c), PRECISION[precision],
                           int(bool(explicit_restrict_residual)), OUTER[outer], int(bool(use_graph)),
-                          int(bool(skip_square_levels)))
+                          int(bool(skip_square_levels)), CYCLE[cycle])
 
     def vcycle(self, x0, r1, **kw):
+        _expect(x0, self.n, "x0", dev=self.device)
+        _expect(r1, self.n, "r1", dev=self.device)
         x = _like(x0, self.n)
         o = self._opts(**kw)
         _check(self._lib.h2mg_vcycle(self._h, _ptr(x0), _ptr(r1), _ptr(x), ctypes.byref(o), _stream()))
@@ -343,9 +414,13 @@ class H2Matrix:
         """Solve A x = b by H2-MG (Algorithm 1 repeated) for a vector or an (n, nrhs)
         block of columns, solved together in groups of four. Returns (x, info): one
         SolveInfo for a vector, a list with one per column for a block."""
+        _expect(b, self.n, "b", cols=True, dev=self.device)
         bb, nrhs = _colmajor(b)
         if x is None:
             x = _new_cols(b, self.n, None if len(b.shape) == 1 else nrhs)
+        _expect(x, self.n, "x", cols=True, dev=self.device)
+        if tuple(x.shape) != tuple(b.shape):
+            raise ValueError(f"x must have the shape of b {tuple(b.shape)}, got {tuple(x.shape)}")
         xb, _ = _colmajor(x)
         o = self._opts(**kw)
         infos = (SolveInfo * nrhs)()
@@ -359,54 +434,57 @@ class H2Matrix:
 # --------------------------------------------------------------------------- adjoint
 class MaternLoss:
     """L(y, b, length, nugget) = 1/2 y^T K^{-1} y + 1^T K^{-1} b for the Matern-3/2 kernel
-    matrix K = (1 + sqrt3 r/l) exp(-sqrt3 r/l) + s I in H2 form, with gradients by the
-    adjoint method: dL/dy = K^{-1} y, dL/db = K^{-1} 1 (one extra H2-MG solve, K being
-    symmetric), dL/dtheta = -1/2 a^T (dK/dtheta) a - w^T (dK/dtheta) x with a = K^{-1} y,
-    x = K^{-1} b, w = K^{-1} 1; dK/dl is the H2 sibling of K with the derivative kernel
-    and dK/ds = I. The forward pass solves for y, b and (when a gradient is wanted) the
-    ones vector together as one three-column H2-MG solve; the backward pass applies
-    dK/dl to a and x as one two-column product. Only the solution vectors are kept
-    between forward and backward."""
+    matrix K = (1 + sqrt3 r/l) exp(-sqrt3 r/l) + s I in H2 form, as a torch.autograd
+    function. The loss and its adjoint gradients (dL/dy = K^{-1} y, dL/db = K^{-1} 1,
+    dL/dl and dL/ds through the derivative sibling dK/dl and dK/ds = I) come from one
+    library call (h2mg_matern_loss_grad): this class only marshals arguments and scales
+    the stored gradients by the incoming one. The forward pass builds K (and dK/dl when
+    a gradient is wanted) and keeps only the gradient vectors and scalars."""
 
     @staticmethod
     def apply(points, y, b, length, nugget, leaf=64, q=4, eta=1.0, tol=1e-12, max_cycles=200,
-              outer="fcg", n_f=1, n_c=40, precision="f64", use_graph=False):
+              outer="fcg", n_f=1, n_c=40, precision="f64", use_graph=False, basis="chebyshev",
+              basis_tol=1e-9, cycle="V"):
         """``precision="mixed_f32"`` runs the V-cycles on an FP32 copy inside the float64
-        outer loop (the solutions still meet ``tol`` in float64)."""
+        outer loop (the solutions still meet ``tol`` in float64); ``basis="skeleton"``
+        builds K (and so dK/dl, on the same skeletons) to the tolerance ``basis_tol``."""
         import torch
 
         class _Fn(torch.autograd.Function):
             @staticmethod
             def forward(ctx, y_, b_, l_, s_):
                 K = H2Matrix(points, "matern32", length=float(l_), nugget=float(s_), leaf=leaf, q=q, eta=eta,
-                             with_f32=(precision == "mixed_f32"))
-                kw = dict(tol=tol, max_cycles=max_cycles, outer=outer, n_f=n_f, n_c=n_c, precision=precision,
-                          use_graph=use_graph)
-                yd = y_.detach().contiguous()
-                ones = torch.ones_like(yd)
-                cols = [yd, b_.detach(), ones] if any(ctx.needs_input_grad) else [yd, b_.detach()]
-                B = torch.stack(cols).t()                       # (n, 2 or 3), column-major
-                S, _ = K.solve(B, **kw)
-                a, x = S[:, 0].contiguous(), S[:, 1].contiguous()
-                loss = 0.5 * dot(yd, a) + dot(x, ones)
-                ctx.K, ctx.l = K, float(l_)
-                w = S[:, 2].contiguous() if len(cols) == 3 else torch.empty(0, dtype=a.dtype, device=a.device)
-                ctx.save_for_backward(a, x, w)
-                return torch.tensor(loss, dtype=torch.float64, device=y_.device)
+                             with_f32=(precision == "mixed_f32"), basis=basis, basis_tol=basis_tol)
+                want = any(ctx.needs_input_grad)
+                dK = K.sibling("dmatern32_dl", length=float(l_)) if want else None
+                o = H2Matrix._opts(tol=tol, max_cycles=max_cycles, outer=outer, n_f=n_f, n_c=n_c,
+                                   precision=precision, use_graph=use_graph, cycle=cycle)
+                yd, bd = y_.detach().contiguous(), b_.detach().contiguous()
+                _expect(yd, K.n, "y", dev=K.device)
+                _expect(bd, K.n, "b", dev=K.device)
+                loss, dl, ds = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+                gy = torch.empty_like(yd) if want else None
+                gb = torch.empty_like(yd) if want else None
+                infos = (SolveInfo * 3)()
+                st = K._lib.h2mg_matern_loss_grad(K._h, dK._h if dK is not None else None, _ptr(yd), _ptr(bd),
+                                                  ctypes.byref(o), ctypes.byref(loss), _ptr(gy), _ptr(gb),
+                                                  ctypes.byref(dl) if want else None,
+                                                  ctypes.byref(ds) if want else None, infos, _stream())
+                if dK is not None:
+                    dK.close()
+                K.close()
+                _check(st)
+                ctx.save_for_backward(*(v for v in (gy, gb) if v is not None))
+                ctx.scalars = (dl.value, ds.value) if want else None
+                return torch.tensor(loss.value, dtype=torch.float64, device=y_.device)
 
             @staticmethod
             def backward(ctx, g):
-                a, x, w = ctx.saved_tensors
-                K = ctx.K
-                dK = K.sibling("dmatern32_dl", length=ctx.l)
-                P = dK.apply(torch.stack([a, x]).t())
-                dKa, dKx = P[:, 0].contiguous(), P[:, 1].contiguous()
-                dl = -0.5 * dot(a, dKa) - dot(w, dKx)
-                ds = -0.5 * dot(a, a) - dot(w, x)
-                dK.close()
+                gy, gb = ctx.saved_tensors
                 gv = float(g)
-                dev = a.device
-                return (gv * a, gv * w, torch.tensor(gv * dl, dtype=torch.float64, device=dev),
+                dl, ds = ctx.scalars
+                dev = gy.device
+                return (gv * gy, gv * gb, torch.tensor(gv * dl, dtype=torch.float64, device=dev),
                         torch.tensor(gv * ds, dtype=torch.float64, device=dev))
 
         return _Fn.apply(y, b, length, nugget)
@@ -417,8 +495,14 @@ def solve_batched(mats, bs, xs=None, raise_on_fail: bool = True, **kw):
     the V-cycles of all problems run from one graph launch per outer iteration when
     ``use_graph=True``. Returns (xs, [SolveInfo per problem])."""
     P = len(mats)
+    if len(bs) != P or (xs is not None and len(xs) != P):
+        raise ValueError("need one right-hand side (and one x) per matrix")
+    for m, b in zip(mats, bs):
+        _expect(b, m.n, "b", dev=m.device)
     if xs is None:
         xs = [_like(b, int(b.shape[0])) for b in bs]
+    for m, x in zip(mats, xs):
+        _expect(x, m.n, "x", dev=m.device)
     arr = ctypes.c_void_p * P
     hs = arr(*[m._h.value for m in mats])
     bp = arr(*[_ptr(b) for b in bs])

@@ -785,13 +785,16 @@ void setup_operators(Matrix& M) {
 }
 
 template <int FMT, int NR>
-static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, void* yrow, cudaStream_t s) {
+static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, void* yrow, cudaStream_t s,
+                          int force_split = 0) {
   using vt = typename Ar<FMT>::vec_t;
   using yt = typename Ar<FMT>::yo_t;
   if (op.nrows == 0) return;
   H2_CUDA(cudaMemsetAsync(yrow, 0, sizeof(yt) * (size_t)op.nrows * op.K * NR, s));
-  // enough CTAs to fill the GPU when the operator has few block rows
-  const int split = std::max(1, std::min(16, ceil_div(2048, op.nrows)));
+  // CTAs per block row: the autotuner's choice, else enough CTAs to fill the GPU when
+  // the operator has few block rows
+  const int tuned = op.split[FMT][nr_index(NR)];
+  const int split = force_split > 0 ? force_split : (tuned > 0 ? tuned : split_heuristic(op.nrows));
   const int grid = op.nrows * split;
   const void* const* blk = f32 ? op.blk32 : op.blk;
   Profile& P = M.prof;
@@ -995,6 +998,87 @@ void apply_level1_ws(Matrix& M, const double* x, double* y, cudaStream_t s, cons
 void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts) {
   *coef = 8 * (size_t)std::max(M.nslots(), 1) * M.KC;
   *pts = 8 * (size_t)(1 << M.L) * M.KD;
+}
+
+// ----------------------------------------------------------------------------- autotuner
+// Times `reps` launches of one block product with row split `split` on the handle's
+// workspaces (contents irrelevant: only the launch time is wanted).
+template <int FMT, int NR>
+static float time_product(Matrix& M, SymOp& op, bool pts, int split, int reps, cudaStream_t s, cudaEvent_t e0,
+                          cudaEvent_t e1) {
+  const bool f32 = FMT == FMT_F32;
+  void* x = pts ? M.wxp.p : M.wx.p;
+  void* y = pts ? M.wyp.p : M.wyrow.p;
+  launch_bsgemv<FMT, NR>(M, op, f32, x, y, s, split);   // warm-up
+  H2_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) launch_bsgemv<FMT, NR>(M, op, f32, x, y, s, split);
+  H2_CUDA(cudaEventRecord(e1, s));
+  H2_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  return ms / reps;
+}
+
+template <int FMT, int NR>
+static void tune_one(Matrix& M, SymOp& op, bool pts, int opi, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                     std::vector<double>& rep) {
+  if (op.nrows == 0 || op.nnz == 0) return;
+  const int heur = split_heuristic(op.nrows);
+  const int cands[] = {1, 2, 4, 8, 16, 32, 64};
+  const float base = time_product<FMT, NR>(M, op, pts, heur, 3, s, e0, e1);
+  float best = base;
+  int bs = heur;
+  for (int c : cands) {
+    if (c == heur || (int64_t)op.nrows * c > (1 << 22)) continue;
+    if (c > 1 && op.nnz < op.nrows * c) continue;       // more CTAs than blocks: idle CTAs
+    const float t = time_product<FMT, NR>(M, op, pts, c, 3, s, e0, e1);
+    if (t < best) {
+      best = t;
+      bs = c;
+    }
+  }
+  op.split[FMT][nr_index(NR)] = bs;
+  rep.insert(rep.end(), {(double)opi, (double)NR, (double)base, (double)best});
+}
+
+// Every operator of the hierarchy (index 0 = the close part of level 1, i = the
+// coupling operator of level i), in the primary format for 1 and 2 columns and, with
+// an FP32 copy, in FP32 for 1, 2 and 4 columns.
+int autotune_products(Matrix& M, cudaStream_t s, double* out, int cap) {
+  H2_REQUIRE(!M.prof.on, H2MG_ERR_INVALID_ARG, "stop h2mg_profile before tuning");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  H2_CUDA(cudaEventCreate(&e0));
+  H2_CUDA(cudaEventCreate(&e1));
+  std::vector<double> rep;
+  try {
+    for (int oi = 0; oi < (int)M.opC.size(); ++oi) {
+      SymOp& op = oi == 0 ? M.opD : M.opC[oi];
+      const bool pts = oi == 0;
+      if (M.fmt == FMT_DF) {
+        tune_one<FMT_DF, 1>(M, op, pts, oi, s, e0, e1, rep);
+        tune_one<FMT_DF, 2>(M, op, pts, oi, s, e0, e1, rep);
+      } else {
+        tune_one<FMT_F64, 1>(M, op, pts, oi, s, e0, e1, rep);
+        tune_one<FMT_F64, 2>(M, op, pts, oi, s, e0, e1, rep);
+      }
+      if (M.with_f32 && op.blk32) {
+        tune_one<FMT_F32, 1>(M, op, pts, oi, s, e0, e1, rep);
+        tune_one<FMT_F32, 2>(M, op, pts, oi, s, e0, e1, rep);
+        tune_one<FMT_F32, 4>(M, op, pts, oi, s, e0, e1, rep);
+      }
+    }
+  } catch (...) {
+    best_effort(cudaEventDestroy(e0), "cudaEventDestroy (tune)");
+    best_effort(cudaEventDestroy(e1), "cudaEventDestroy (tune)");
+    throw;
+  }
+  best_effort(cudaEventDestroy(e0), "cudaEventDestroy (tune)");
+  best_effort(cudaEventDestroy(e1), "cudaEventDestroy (tune)");
+  const int n = (int)rep.size() / 4;
+  if (out)
+    for (int k = 0; k < std::min(n, cap); ++k)
+      for (int j = 0; j < 4; ++j) out[4 * k + j] = rep[4 * k + j];
+  return n;
 }
 
 // Algorithmic bytes of one A_i apply in the primary format: every stored block once,

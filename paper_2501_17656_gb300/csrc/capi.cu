@@ -33,6 +33,19 @@ void* Matrix::alloc(size_t bytes) {
   return p;
 }
 
+void Matrix::free_owned(void* p) {
+  if (!p) return;
+  for (auto& d : owned)
+    if (d.p == p) {
+      // queued work of the handle's stream may still use it
+      best_effort(cudaStreamSynchronize(stream), "cudaStreamSynchronize (free)");
+      best_effort(cudaFree(d.p), "cudaFree (build scratch)");
+      d.p = nullptr;
+      d.bytes = 0;
+      return;
+    }
+}
+
 void best_effort(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return;
   if (std::getenv("H2MG_DEBUG")) std::fprintf(stderr, "[h2mg] %s failed: %s\n", what, cudaGetErrorString(e));
@@ -189,6 +202,7 @@ static void build_sibling(Matrix& B, const Matrix& A, const h2mg_kernel* k) {
   cudaStream_t s = B.stream;
   B.n = A.n; B.dim = A.dim; B.leaf = A.leaf; B.q = A.q; B.k = A.k; B.eta = A.eta;
   B.fmt = A.fmt; B.with_f32 = false; B.apply_only = true;
+  B.basis = A.basis; B.basis_tol = A.basis_tol; B.d_nsw = A.d_nsw; B.d_skel = A.d_skel;
   B.L = A.L; B.KD = A.KD; B.KC = A.KC; B.tstar = A.tstar; B.lev_nat = A.lev_nat; B.lev = 1;
   B.offsets = A.offsets; B.far = A.far; B.inadm = A.inadm; B.h_rank = A.h_rank;
   B.d_perm = A.d_perm; B.d_slot_of = A.d_slot_of; B.d_leafoff = A.d_leafoff; B.d_X = A.d_X;
@@ -258,10 +272,19 @@ h2mg_status h2mg_build(const double* points, int64_t n, int dim, const h2mg_kern
     H2_REQUIRE(n >= 1 && n <= (1ll << 30), H2MG_ERR_INVALID_ARG, "n must be in [1, 2^30]");
     H2_REQUIRE(dim >= 1 && dim <= 3, H2MG_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
     H2_REQUIRE(o->leaf_size >= 2 && o->leaf_size <= 64, H2MG_ERR_INVALID_ARG, "leaf_size must be in [2, 64]");
-    H2_REQUIRE(o->cheb_q >= 1, H2MG_ERR_INVALID_ARG, "cheb_q must be >= 1");
+    H2_REQUIRE(o->basis == H2MG_BASIS_CHEBYSHEV || o->basis == H2MG_BASIS_SKELETON, H2MG_ERR_INVALID_ARG,
+               "basis must be H2MG_BASIS_CHEBYSHEV or H2MG_BASIS_SKELETON");
     int kk = 1;
-    for (int d = 0; d < dim; ++d) kk *= o->cheb_q;
-    H2_REQUIRE(kk <= 64, H2MG_ERR_UNSUPPORTED, "rank q^dim must be <= 64");
+    if (o->basis == H2MG_BASIS_CHEBYSHEV) {
+      H2_REQUIRE(o->cheb_q >= 1, H2MG_ERR_INVALID_ARG, "cheb_q must be >= 1");
+      for (int d = 0; d < dim; ++d) kk *= o->cheb_q;
+      H2_REQUIRE(kk <= 64, H2MG_ERR_UNSUPPORTED, "rank q^dim must be <= 64");
+    } else {
+      H2_REQUIRE(o->rank_max >= 1 && o->rank_max <= 64, H2MG_ERR_INVALID_ARG, "rank_max must be in [1, 64]");
+      H2_REQUIRE(o->basis_tol >= 0.0 && std::isfinite(o->basis_tol), H2MG_ERR_INVALID_ARG,
+                 "basis_tol must be finite and >= 0");
+      kk = o->rank_max;
+    }
     H2_REQUIRE(o->eta >= 0.0 && std::isfinite(o->eta), H2MG_ERR_INVALID_ARG, "eta must be finite and >= 0");
     H2_REQUIRE(o->storage == H2MG_STORE_F64 || o->storage == H2MG_STORE_DF64, H2MG_ERR_INVALID_ARG,
                "storage must be H2MG_STORE_F64 or H2MG_STORE_DF64");
@@ -284,6 +307,8 @@ h2mg_status h2mg_build(const double* points, int64_t n, int dim, const h2mg_kern
     M.q = o->cheb_q;
     M.k = kk;
     M.eta = o->eta;
+    M.basis = o->basis;
+    M.basis_tol = o->basis_tol;
     M.fmt = o->storage == H2MG_STORE_DF64 ? FMT_DF : FMT_F64;
     M.with_f32 = o->with_f32 != 0;
     M.stream = (cudaStream_t)stream;
@@ -329,6 +354,8 @@ h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int6
     H2_REQUIRE(nrhs >= 1 && ld >= M.n, H2MG_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= n");
     H2_REQUIRE(o->max_cycles >= 0 && o->n_f >= 0 && o->n_c >= 0 && o->tol >= 0, H2MG_ERR_INVALID_ARG,
                "bad solve options");
+    H2_REQUIRE(o->outer >= H2MG_OUTER_VCYCLE && o->outer <= H2MG_OUTER_CG, H2MG_ERR_INVALID_ARG, "unknown outer loop");
+    H2_REQUIRE(o->cycle >= H2MG_CYCLE_V && o->cycle <= H2MG_CYCLE_F, H2MG_ERR_INVALID_ARG, "unknown cycle type");
     H2_REQUIRE(o->precision == H2MG_PREC_F64 || (o->precision == H2MG_PREC_MIXED_F32 && M.with_f32),
                H2MG_ERR_INVALID_ARG, "mixed precision needs a matrix built with_f32");
     H2_REQUIRE(!M.apply_only, H2MG_ERR_INVALID_ARG, "matrix was built for products only");
@@ -356,6 +383,9 @@ h2mg_status h2mg_solve_batched(int nprob, const h2mg_matrix* A, const double* co
     H2_REQUIRE(nprob >= 1 && A && b && x && o && info, H2MG_ERR_INVALID_ARG, "null pointer argument");
     H2_REQUIRE(o->max_cycles >= 0 && o->n_f >= 0 && o->n_c >= 0 && o->tol >= 0, H2MG_ERR_INVALID_ARG,
                "bad solve options");
+    H2_REQUIRE(o->outer == H2MG_OUTER_VCYCLE || o->outer == H2MG_OUTER_FCG, H2MG_ERR_INVALID_ARG,
+               "the batched solve runs repeated cycles or flexible CG");
+    H2_REQUIRE(o->cycle >= H2MG_CYCLE_V && o->cycle <= H2MG_CYCLE_F, H2MG_ERR_INVALID_ARG, "unknown cycle type");
     std::vector<Matrix*> Ms(nprob);
     for (int p = 0; p < nprob; ++p) {
       H2_REQUIRE(A[p] && b[p] && x[p], H2MG_ERR_INVALID_ARG, "null pointer argument");
@@ -476,6 +506,18 @@ h2mg_status h2mg_export(h2mg_matrix A, int what, int arg, void* buf, int64_t cap
         put_ints(v);
         break;
       }
+      case H2MG_X_SKELETON: {
+        H2_REQUIRE(M.basis == H2MG_BASIS_SKELETON && M.d_skel, H2MG_ERR_INVALID_ARG, "matrix has no skeletons");
+        H2_REQUIRE(M.tstar >= 0 && arg >= M.tstar && arg <= M.L, H2MG_ERR_INVALID_ARG, "level has no basis");
+        std::vector<int> v((size_t)64 << arg), perm(M.n);
+        H2_CUDA(cudaMemcpy(v.data(), M.d_skel + (size_t)M.slot0(arg) * 64, sizeof(int) * v.size(),
+                           cudaMemcpyDeviceToHost));
+        H2_CUDA(cudaMemcpy(perm.data(), M.d_perm, sizeof(int) * M.n, cudaMemcpyDeviceToHost));
+        for (auto& e : v)
+          if (e >= 0) e = perm[e];
+        put_ints(v);
+        break;
+      }
       case H2MG_X_BOXES: {
         H2_REQUIRE(arg >= 0 && arg <= M.L, H2MG_ERR_INVALID_ARG, "level out of range");
         size_t nb = sizeof(double) * 2 * M.dim * (1 << arg);
@@ -550,6 +592,7 @@ h2mg_status h2mg_vcycle(h2mg_matrix A, const double* x0, const double* r1, doubl
                         const h2mg_solve_opts* o, void* stream) {
   return guard([&]() -> h2mg_status {
     H2_REQUIRE(A && x0 && r1 && x_out && o, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    H2_REQUIRE(o->cycle >= H2MG_CYCLE_V && o->cycle <= H2MG_CYCLE_F, H2MG_ERR_INVALID_ARG, "unknown cycle type");
     Matrix& M = A->M;
     H2_REQUIRE(!M.apply_only, H2MG_ERR_INVALID_ARG, "matrix was built for products only");
     if (!M.coarse_ok) throw Error{H2MG_ERR_NOT_SPD, "the coarsest operator is not positive definite"};
@@ -612,6 +655,16 @@ h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* m
   });
 }
 
+h2mg_status h2mg_autotune(h2mg_matrix A, void* stream, double* report, int cap, int* count) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && cap >= 0 && (report || cap == 0), H2MG_ERR_INVALID_ARG, "bad argument");
+    Matrix& M = A->M;
+    const int n = autotune_products(M, (cudaStream_t)stream, report, cap);
+    if (count) *count = n;
+    return H2MG_OK;
+  });
+}
+
 h2mg_status h2mg_build_sibling(h2mg_matrix A, const h2mg_kernel* k, void* stream, h2mg_matrix* out) {
   if (out) *out = nullptr;
   return guard([&]() -> h2mg_status {
@@ -633,6 +686,99 @@ h2mg_status h2mg_build_sibling(h2mg_matrix A, const h2mg_kernel* k, void* stream
       throw;
     }
     *out = h;
+    return H2MG_OK;
+  });
+}
+
+__global__ void k_fill(double* __restrict__ v, int64_t n, double a) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = a;
+}
+
+h2mg_status h2mg_matern_loss_grad(h2mg_matrix K, h2mg_matrix dK, const double* y, const double* b,
+                                  const h2mg_solve_opts* o, double* loss, double* dLdy, double* dLdb, double* dLdl,
+                                  double* dLds, h2mg_solve_info* info, void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(K && y && b && o && loss, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = K->M;
+    H2_REQUIRE(M.kp.kind == H2MG_K_MATERN32 && !M.apply_only, H2MG_ERR_INVALID_ARG,
+               "K must be a Matern-3/2 matrix built for solves");
+    H2_REQUIRE(!M.has_weights && !M.has_diag, H2MG_ERR_INVALID_ARG, "K must have no weights or diagonal override");
+    const bool want_l = dLdl != nullptr;
+    H2_REQUIRE(!want_l || dK, H2MG_ERR_INVALID_ARG, "dL/dl needs the derivative matrix dK");
+    if (dK) {
+      const Matrix& D = dK->M;
+      H2_REQUIRE(D.apply_only && D.kp.kind == H2MG_K_DMATERN32_DL && D.d_perm == M.d_perm &&
+                     D.kp.length == M.kp.length,
+                 H2MG_ERR_INVALID_ARG, "dK must be the d/dlength sibling of K (same length)");
+    }
+    H2_REQUIRE(o->outer >= H2MG_OUTER_VCYCLE && o->outer <= H2MG_OUTER_CG && o->cycle >= H2MG_CYCLE_V &&
+                   o->cycle <= H2MG_CYCLE_F && o->max_cycles >= 0 && o->tol >= 0,
+               H2MG_ERR_INVALID_ARG, "bad solve options");
+    H2_REQUIRE(o->precision == H2MG_PREC_F64 || (o->precision == H2MG_PREC_MIXED_F32 && M.with_f32),
+               H2MG_ERR_INVALID_ARG, "mixed precision needs a matrix built with_f32");
+    if (!M.coarse_ok) throw Error{H2MG_ERR_NOT_SPD, "the coarsest operator is not positive definite"};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = M.n;
+    const bool want_w = dLdb || dLdl || dLds;
+    const int nr = want_w ? 3 : 2;
+    // columns [y, b, 1] and their solutions [a, x, w], packed column-major
+    struct Tmp {
+      void* p = nullptr;
+      ~Tmp() {
+        if (p) best_effort(cudaFree(p), "cudaFree (loss)");
+      }
+    } tb, ts, tq;
+    H2_CUDA(cudaMalloc(&tb.p, sizeof(double) * n * nr));
+    H2_CUDA(cudaMalloc(&ts.p, sizeof(double) * n * nr));
+    H2_CUDA(cudaMalloc(&tq.p, sizeof(double) * n * 2));
+    double* B = (double*)tb.p;
+    double* X = (double*)ts.p;
+    double* Q = (double*)tq.p;
+    H2_CUDA(cudaMemcpyAsync(B, y, sizeof(double) * n, cudaMemcpyDefault, s));
+    H2_CUDA(cudaMemcpyAsync(B + n, b, sizeof(double) * n, cudaMemcpyDefault, s));
+    if (want_w) {
+      { k_fill<<<ceil_div(n, 256), 256, 0, s>>>(B + 2 * n, n, 1.0); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+    }
+    H2_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * n * nr, s));
+    h2mg_solve_info inf[NRMAX];
+    const h2mg_status st = solve_multi(M, B, X, nr, *o, inf, s);     // a, x (and w) to tol
+    if (info)
+      for (int c = 0; c < nr; ++c) info[c] = inf[c];
+    if (st != H2MG_OK) {
+      set_error(h2mg_error_string(st));
+      return st;
+    }
+    const double* a = X;
+    const double* x = X + n;
+    const double* w = X + 2 * n;
+    double ya, ox;
+    dots(M, B, a, n, 1, &ya, s);                                      // y^T a
+    dots(M, B + 2 * n, x, n, 1, &ox, s);                              // 1^T x (the ones column)
+    if (!want_w) {
+      // 1^T x without the ones column: x against a ones vector written into Q
+      { k_fill<<<ceil_div(n, 256), 256, 0, s>>>(Q, n, 1.0); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+      dots(M, Q, x, n, 1, &ox, s);
+    }
+    *loss = 0.5 * ya + ox;                                            // L = 1/2 y^T K^-1 y + 1^T K^-1 b
+    if (dLdy) H2_CUDA(cudaMemcpyAsync(dLdy, a, sizeof(double) * n, cudaMemcpyDefault, s));   // dL/dy = a
+    if (dLdb) H2_CUDA(cudaMemcpyAsync(dLdb, w, sizeof(double) * n, cudaMemcpyDefault, s));   // dL/db = w
+    if (dLds) {                                                       // dK/ds = I
+      double aa, wx;
+      dots(M, a, a, n, 1, &aa, s);
+      dots(M, w, x, n, 1, &wx, s);
+      *dLds = -0.5 * aa - wx;
+    }
+    if (want_l) {                                                     // dK/dl: the sibling's product
+      apply_level_multi(dK->M, 1, false, X, n, Q, n, 2, s);           // [dK a, dK x]
+      double adka, wdkx;
+      dots(M, a, Q, n, 1, &adka, s);
+      dots(M, w, Q + n, n, 1, &wdkx, s);
+      *dLdl = -0.5 * adka - wdkx;
+    }
+    H2_CUDA(cudaStreamSynchronize(s));
     return H2MG_OK;
   });
 }

@@ -210,10 +210,13 @@ __global__ void k_nodes(const double* __restrict__ box, int ell, int dim, int q,
 }
 
 // ----------------------------------------------------------------------------- leaf QR
-// One block per leaf: U^cheb (n_j x k) -> Q into U (KD x KC), R into Rout (KC x KC).
+// One block per leaf: U^0 (n_j x k) -> Q into U (KD x KC), R into Rout (KC x KC).
+// U^0 is the Chebyshev basis sqrt(w_i) L_a(x_i), or, with skeleton factors Tid
+// (column-major, ld 128 per leaf, rank_id[j] columns), the leaf's interpolation matrix.
 __global__ void k_leaf_qr(const double* __restrict__ X, const double* __restrict__ sw,
                           const int* __restrict__ leafoff, const double* __restrict__ box,
                           int dim, int q, int k, int KD, int KC, double floor_hw,
+                          const double* __restrict__ Tid, const int* __restrict__ rank_id,
                           double* __restrict__ U, double* __restrict__ Rout) {
   extern __shared__ double sm[];
   double* A = sm;                    // KD x k
@@ -222,12 +225,17 @@ __global__ void k_leaf_qr(const double* __restrict__ X, const double* __restrict
   double* red = tau + 64;            // 33
   int j = blockIdx.x;
   int p0 = leafoff[j], m = leafoff[j + 1] - p0;
+  if (Tid) k = rank_id[j];
   double cen[3], hw[3];
   box_center_half(box, j, dim, floor_hw, cen, hw);
   for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
     int i = e % m, a = e / m;
-    const double* x = X + (int64_t)(p0 + i) * dim;
-    A[i + a * KD] = sw[p0 + i] * lagrange_tensor(a, x, cen, hw, dim, q);
+    if (Tid) {
+      A[i + a * KD] = Tid[(int64_t)j * 128 * 64 + i + a * 128];
+    } else {
+      const double* x = X + (int64_t)(p0 + i) * dim;
+      A[i + a * KD] = sw[p0 + i] * lagrange_tensor(a, x, cen, hw, dim, q);
+    }
   }
   __syncthreads();
   cta_qr(A, KD, m, k, Qm, KD, tau, red);
@@ -247,9 +255,13 @@ __global__ void k_leaf_qr(const double* __restrict__ X, const double* __restrict
 // ----------------------------------------------------------------------------- parent QR
 // One block per parent p at level ell: M = [R_c1 E_c1; R_c2 E_c2] = Q R_P; the
 // orthonormal transfers E'_c are the row blocks of Q (stored KC x KC, child rows).
+// E_c is the Chebyshev transfer L^P_b(xi^c_a) (k x k), or, with skeleton factors
+// (Tid: the parent's interpolation matrix, ld 128, rows = the children's skeletons),
+// the rows of T_p that belong to child c (r_c x r_p).
 __global__ void k_parent_qr(const double* __restrict__ box_p, const double* __restrict__ nodes_c,
                             const int* __restrict__ rank_c, int dim, int q, int k, int KC,
                             double floor_hw, const double* __restrict__ R_c,
+                            const double* __restrict__ Tid, const int* __restrict__ rank_p,
                             double* __restrict__ E_out, double* __restrict__ R_out) {
   extern __shared__ double sm[];
   double* E = sm;                    // k x k (one child at a time)
@@ -262,24 +274,28 @@ __global__ void k_parent_qr(const double* __restrict__ box_p, const double* __re
   box_center_half(box_p, p, dim, floor_hw, cen, hw);
   int r1 = rank_c[2 * p], r2 = rank_c[2 * p + 1];
   int m = r1 + r2, ld = 2 * k;
+  const int kout = Tid ? rank_p[p] : k;   // columns: the parent's basis functions
   for (int c = 0; c < 2; ++c) {
     int child = 2 * p + c;
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-      int a = e % k, b = e / k;   // E_c[a, b] = L^P_b(xi^c_a)
-      E[a + b * k] = lagrange_tensor(b, nodes_c + ((int64_t)child * k + a) * dim, cen, hw, dim, q);
+    int rc = c ? r2 : r1, row0 = c ? r1 : 0;
+    const int kin = Tid ? rc : k;         // rows of E_c: the child's basis functions
+    for (int e = threadIdx.x; e < kin * kout; e += blockDim.x) {
+      int a = e % kin, b = e / kin;
+      E[a + b * kin] = Tid ? Tid[(int64_t)p * 128 * 64 + row0 + a + b * 128]   // E_c[a, b] = T_p[c's a-th, b]
+                           : lagrange_tensor(b, nodes_c + ((int64_t)child * k + a) * dim, cen, hw, dim, q);
     }
     __syncthreads();
     const double* Rc = R_c + (int64_t)child * KC * KC;
-    int rc = c ? r2 : r1, row0 = c ? r1 : 0;
-    for (int e = threadIdx.x; e < rc * k; e += blockDim.x) {
+    for (int e = threadIdx.x; e < rc * kout; e += blockDim.x) {
       int i = e % rc, b = e / rc;
       double s = 0.0;
-      for (int a = i; a < k; ++a) s += Rc[i + a * KC] * E[a + b * k];
+      for (int a = i; a < kin; ++a) s += Rc[i + a * KC] * E[a + b * kin];
       A[row0 + i + b * ld] = s;
     }
     __syncthreads();
   }
-  cta_qr(A, ld, m, k, Qm, ld, tau, red);
+  cta_qr(A, ld, m, kout, Qm, ld, tau, red);
+  k = kout;
   int rp = min(m, k);
   for (int c = 0; c < 2; ++c) {
     int child = 2 * p + c;
@@ -308,26 +324,34 @@ void build_bases(Matrix& M) {
   double ext = 0.0;
   for (int d = 0; d < dim; ++d) ext = std::max(ext, rb[dim + d] - rb[d]);
   double floor_hw = 1e-12 * std::max(ext, 1e-300);
-  // ranks (host): leaves min(k, n_j); parents min(k, r_c1 + r_c2)
-  M.h_rank.assign(nsl, 0);
-  std::vector<int> rk(1 << L);
-  for (int j = 0; j < (1 << L); ++j) rk[j] = std::min(k, M.offsets[L][j + 1] - M.offsets[L][j]);
-  for (int ell = L; ell >= ts; --ell) {
-    if (ell < L) {
-      std::vector<int> up(1 << ell);
-      for (int p = 0; p < (1 << ell); ++p) up[p] = std::min(k, rk[2 * p] + rk[2 * p + 1]);
-      rk.swap(up);
+  const bool skel = M.basis == H2MG_BASIS_SKELETON;
+  if (skel) {
+    // skeletons, interpolation matrices, ranks and coupling points (skeleton.cu)
+    build_skeletons(M);
+  } else {
+    // ranks (host): leaves min(k, n_j); parents min(k, r_c1 + r_c2)
+    M.h_rank.assign(nsl, 0);
+    std::vector<int> rk(1 << L);
+    for (int j = 0; j < (1 << L); ++j) rk[j] = std::min(k, M.offsets[L][j + 1] - M.offsets[L][j]);
+    for (int ell = L; ell >= ts; --ell) {
+      if (ell < L) {
+        std::vector<int> up(1 << ell);
+        for (int p = 0; p < (1 << ell); ++p) up[p] = std::min(k, rk[2 * p] + rk[2 * p + 1]);
+        rk.swap(up);
+      }
+      for (int j = 0; j < (1 << ell); ++j) M.h_rank[M.slot0(ell) + j] = rk[j];
     }
-    for (int j = 0; j < (1 << ell); ++j) M.h_rank[M.slot0(ell) + j] = rk[j];
+    M.d_rank = (int*)M.alloc(sizeof(int) * nsl);
+    H2_CUDA(cudaMemcpyAsync(M.d_rank, M.h_rank.data(), sizeof(int) * nsl, cudaMemcpyHostToDevice, s));
+    M.d_nodes = (double*)M.alloc(sizeof(double) * (size_t)nsl * k * dim);
+    for (int ell = ts; ell <= L; ++ell) {
+      { k_nodes<<<1 << ell, 128, 0, s>>>(M.d_box[ell], ell, dim, q, k, floor_hw,
+                                       M.d_nodes + (size_t)M.slot0(ell) * k * dim); ::h2mg::count_launch(); }
+      H2_LAUNCH_CHECK();
+    }
   }
-  M.d_rank = (int*)M.alloc(sizeof(int) * nsl);
-  H2_CUDA(cudaMemcpyAsync(M.d_rank, M.h_rank.data(), sizeof(int) * nsl, cudaMemcpyHostToDevice, s));
-  M.d_nodes = (double*)M.alloc(sizeof(double) * (size_t)nsl * k * dim);
-  for (int ell = ts; ell <= L; ++ell) {
-    { k_nodes<<<1 << ell, 128, 0, s>>>(M.d_box[ell], ell, dim, q, k, floor_hw,
-                                     M.d_nodes + (size_t)M.slot0(ell) * k * dim); ::h2mg::count_launch(); }
-    H2_LAUNCH_CHECK();
-  }
+  const double* Tid = skel ? (const double*)M.tid.p : nullptr;
+  const int* rid = skel ? M.d_rank : nullptr;
   M.d_U = (double*)M.alloc(sizeof(double) * (size_t)(1 << L) * KD * KC);
   M.d_R = (double*)M.alloc(sizeof(double) * (size_t)nsl * KC * KC);
   M.d_E = (double*)M.alloc(sizeof(double) * (size_t)nsl * KC * KC);
@@ -335,7 +359,9 @@ void build_bases(Matrix& M) {
     size_t sm = sizeof(double) * ((size_t)KD * k + KD * KD + 64 + 33);
     H2_CUDA(cudaFuncSetAttribute(k_leaf_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     { k_leaf_qr<<<1 << L, 128, sm, s>>>(M.d_X, M.d_sw, M.d_leafoff, M.d_box[L], dim, q, k, KD, KC,
-                                       floor_hw, M.d_U, M.d_R + (size_t)M.slot0(L) * KC * KC); ::h2mg::count_launch(); }
+                                       floor_hw, Tid ? Tid + (size_t)M.slot0(L) * 128 * 64 : nullptr,
+                                       rid ? rid + M.slot0(L) : nullptr, M.d_U,
+                                       M.d_R + (size_t)M.slot0(L) * KC * KC); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   }
   {
@@ -345,28 +371,38 @@ void build_bases(Matrix& M) {
       { k_parent_qr<<<1 << ell, 128, sm, s>>>(
           M.d_box[ell], M.d_nodes + (size_t)M.slot0(ell + 1) * k * dim, M.d_rank + M.slot0(ell + 1),
           dim, q, k, KC, floor_hw, M.d_R + (size_t)M.slot0(ell + 1) * KC * KC,
+          Tid ? Tid + (size_t)M.slot0(ell) * 128 * 64 : nullptr, rid ? rid + M.slot0(ell) : nullptr,
           M.d_E + (size_t)M.slot0(ell + 1) * KC * KC, M.d_R + (size_t)M.slot0(ell) * KC * KC); ::h2mg::count_launch(); }
       H2_LAUNCH_CHECK();
     }
   }
   H2_CUDA(cudaStreamSynchronize(s));
+  if (skel) M.free_owned(M.tid.p);   // the interpolation matrices live on in U, E and R
+  M.tid = DevBuf{};
 }
 
 // ----------------------------------------------------------------------------- blocks
 // S = R_t k(xi_t, xi_s) R_s^T for far pairs (t, s) (slots), written swizzled.
+// Coupling points: k per slot (Chebyshev nodes, unit weights), or, with cnt / nw given,
+// the cnt[slot] skeleton points of each slot with their sqrt(w).
 __global__ void k_fill_S(const int* __restrict__ pt, const int* __restrict__ ps,
                          const double* __restrict__ nodes, const double* __restrict__ R, int k,
-                         int KC, int dim, KernelParams kp, void* __restrict__ pool, int fmt) {
+                         int KC, int dim, KernelParams kp, const int* __restrict__ cnt,
+                         const double* __restrict__ nw, void* __restrict__ pool, int fmt) {
   extern __shared__ double sm[];
   double* Sc = sm;              // KC x KC
   double* T = Sc + KC * KC;     // KC x KC
   int64_t b = blockIdx.x;
   int t = pt[b], s = ps[b];
+  const int kt = cnt ? cnt[t] : k, ks = cnt ? cnt[s] : k;
   for (int e = threadIdx.x; e < KC * KC; e += blockDim.x) {
     int a = e % KC, c = e / KC;
-    Sc[e] = (a < k && c < k) ? kernel_eval(kp, nodes + ((int64_t)t * k + a) * dim,
-                                           nodes + ((int64_t)s * k + c) * dim, dim)
-                             : 0.0;
+    double v = 0.0;
+    if (a < kt && c < ks) {
+      v = kernel_eval(kp, nodes + ((int64_t)t * k + a) * dim, nodes + ((int64_t)s * k + c) * dim, dim);
+      if (nw) v *= nw[(int64_t)t * k + a] * nw[(int64_t)s * k + c];
+    }
+    Sc[e] = v;
   }
   __syncthreads();
   const double* Rt = R + (int64_t)t * KC * KC;
@@ -581,7 +617,9 @@ void build_blocks(Matrix& M, const Matrix* base) {
   size_t smS = sizeof(double) * 2 * KC * KC;
   H2_CUDA(cudaFuncSetAttribute(k_fill_S, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smS));
   chunked(M.nS, [&](int64_t b0, int nb) {
-    { k_fill_S<<<nb, 256, smS, s>>>(d_st + b0, d_ss + b0, M.d_nodes, M.d_R, k, KC, dim, M.kp,
+    const bool sk = M.basis == H2MG_BASIS_SKELETON;
+    { k_fill_S<<<nb, 256, smS, s>>>(d_st + b0, d_ss + b0, M.d_nodes, M.d_R, sk ? KC : k, KC, dim, M.kp,
+                                  sk ? M.d_rank : nullptr, sk ? M.d_nsw : nullptr,
                                   (char*)M.poolS.p + pool_bytes(b0, KC, M.fmt), M.fmt); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
   });

@@ -29,10 +29,20 @@ struct SymOp {
   const void** blk = nullptr;      // [nnz] block pointers into the primary pool
   const void** blk32 = nullptr;    // [nnz] block pointers into the FP32 pool (or null)
   int64_t noff = 0;       // off-diagonal entries (each adds K transposed partials)
+  // CTAs per block row chosen by the autotuner, per element format (F64, DF, F32) and
+  // column group size (NR = 1, 2, 4); 0 = the fixed heuristic
+  int split[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   int64_t bytes(int eb, int vb) const {   // algorithmic bytes of one product
     return (int64_t)nnz * K * K * eb + (int64_t)nrows * K * vb * 2 + noff * K * vb;
   }
 };
+inline int nr_index(int nr) { return nr >= 4 ? 2 : nr - 1; }
+// Fixed heuristic of the block product: enough CTAs to fill the GPU when the operator
+// has few block rows (at most 16 CTAs per row).
+inline int split_heuristic(int nrows) {
+  const int v = (2048 + nrows - 1) / (nrows > 0 ? nrows : 1);
+  return v < 1 ? 1 : (v > 16 ? 16 : v);
+}
 
 // CUDA events around the launches of the block product (h2mg_profile).
 struct Profile {
@@ -64,8 +74,10 @@ struct Matrix {
   int dim = 0;
   KernelParams kp{};
   bool has_weights = false, has_diag = false;
-  int leaf = 0, q = 0, k = 0;
+  int leaf = 0, q = 0, k = 0;   // k: Chebyshev nodes q^dim, or the rank cap of skeleton bases
   double eta = 0;
+  int basis = H2MG_BASIS_CHEBYSHEV;
+  double basis_tol = 0.0;       // relative tolerance of skeleton bases
   int fmt = FMT_F64;      // primary block format (FMT_F64 or FMT_DF)
   bool with_f32 = false;
   bool apply_only = false;
@@ -84,7 +96,11 @@ struct Matrix {
   double* d_sw = nullptr;      // [n] sqrt(w) in compact tree order
   double* d_dg = nullptr;      // [n] diagonal entries A_ii in compact tree order
   std::vector<double*> d_box;  // per level, [2^ell * 2 * dim] (lo, hi)
-  double* d_nodes = nullptr;   // Chebyshev nodes of clusters at levels tstar..L (heap slots)
+  double* d_nodes = nullptr;   // coupling points of clusters at levels tstar..L (heap slots):
+                               // Chebyshev nodes (k per slot) or skeleton points (KC per slot)
+  double* d_nsw = nullptr;     // skeleton bases: sqrt(w) of each slot's skeleton points (KC per slot)
+  int* d_skel = nullptr;       // skeleton bases: tree positions of each slot's skeleton (64 per slot)
+  DevBuf tid;                  // skeleton bases, during the build: interpolation matrices
   int* d_rank = nullptr;       // ranks per slot (levels tstar..L)
   std::vector<int> h_rank;     // host copy
 
@@ -139,11 +155,14 @@ struct Matrix {
   std::vector<DevBuf> owned;    // everything else
   ~Matrix();
   void* alloc(size_t bytes);    // owned allocation, zero-initialised
+  void free_owned(void* p);     // release an owned allocation before the handle goes
 };
 
 // ---- tree.cu
 void build_tree(Matrix& M, const double* d_points_user);
 void build_partition(Matrix& M);
+// ---- skeleton.cu
+void build_skeletons(Matrix& M);
 // ---- fill.cu
 void build_bases(Matrix& M);
 void build_blocks(Matrix& M, const Matrix* base);
@@ -166,6 +185,10 @@ constexpr int NRMAX = 4;
 void apply_level_multi(Matrix& M, int i, bool f32, const double* x, int64_t ldx, double* y, int64_t ldy, int nr,
                        cudaStream_t s);
 int64_t apply_bytes(const Matrix& M, int i);
+// Autotuner of the block product: per operator, format and column group, the row
+// split of the fastest timed trial. out (cap entries of 4 doubles) receives
+// (operator index, nr, fixed-heuristic ms, tuned ms) per tuned combination.
+int autotune_products(Matrix& M, cudaStream_t s, double* out, int cap);
 // ---- solve.cu
 void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n, double* x,
             double* r, cudaStream_t s);
@@ -187,6 +210,9 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
 h2mg_status solve_batched(const std::vector<Matrix*>& Ms, const double* const* b, double* const* x,
                           const h2mg_solve_opts& o, h2mg_solve_info* info, cudaStream_t s);
 int64_t level_size(const Matrix& M, int i);
+// out[c] = a_c^T b_c for nr columns of length n (leading dimension n), reduced on the
+// device; the nr results are read back (synchronises s).
+void dots(Matrix& M, const double* a, const double* b, int64_t n, int nr, double* out, cudaStream_t s);
 double device_dot(const double* a, const double* b, int64_t n, cudaStream_t s);
 
 // ---- sort.cu (device primitives)

@@ -2,9 +2,9 @@
 // a fixed device array instead of memory the library allocates.
 //
 // Some callers cannot call cudaMalloc at the point where they need a product: code
-// running while a stream is being captured into a CUDA graph, code inside an
-// allocator callback, or processes whose device memory is entirely reserved up front
-// by another allocator (a framework's caching pool). This entry point allocates
+// inside an allocator callback (which must not re-enter the allocator), or processes
+// whose device memory is entirely reserved up front by another allocator (a
+// framework's caching pool), where a cudaMalloc would fail. This entry point allocates
 // nothing: the product's workspace (coefficient buffers, point buffers and the row
 // accumulators of the block products) lives in the file-scope array below, whose
 // address is looked up once per device.
@@ -69,9 +69,9 @@ extern "C" h2mg_status h2mg_apply_noalloc(h2mg_matrix A, const double* x, double
     ws.yc = p; p += up256(coef);
     ws.xp = p; p += up256(pts);
     ws.yp = p;
-    // padded point slots are read as zeros by the block product; earlier calls may
-    // have left other values there
-    H2_CUDA(cudaMemsetAsync(ws.xp, 0, pts, s));
+    // The point buffer's padded slots must read as zero; the level-1 product clears
+    // that buffer itself before filling it, so what an earlier call left in the array
+    // does not leak into this one.
     bool prof = M.prof.on;
     M.prof.on = false;   // the event record could grow; keep this call allocation-free
     try {

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -140,6 +141,16 @@ __global__ void k_axpy_cols(const double* __restrict__ a, const double* __restri
   y += c * ld;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = fma(al, x[i], y[i]);
+}
+// y_c = x_c + b[c] y_c for every column c = blockIdx.y (b in device memory)
+__global__ void k_xpby_cols(const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ y,
+                            int64_t n, int64_t ld) {
+  const int c = blockIdx.y;
+  const double be = b[c];
+  x += c * ld;
+  y += c * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(be, y[i], x[i]);
 }
 // z = x - y
 __global__ void k_sub(const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ z, int64_t n) {
@@ -386,42 +397,44 @@ static bool square_level(const Matrix& M, int i) {
   return true;
 }
 
-// e_1 of one V-cycle of Algorithm 1 for nr columns of r_1 (n x nr, leading
-// dimension n), into the level-1 error buffer W.et[1]. No host synchronisation and no
-// allocation: the sequence can be captured into a CUDA graph.
-static void vcycle_core(Matrix& M, const h2mg_solve_opts& o, const double* r1, int nr, cudaStream_t s) {
-  H2_REQUIRE(nr >= 1 && nr <= NRMAX, H2MG_ERR_INVALID_ARG, "too many columns for one V-cycle");
+// One visit of level i in a multigrid cycle of type `kind` on A_i e = f (nr columns,
+// leading dimension N_i), into W.et[i]; the first visit starts from zero, later ones
+// from W.et[i] as the previous visit left it. Level l solves directly. Otherwise:
+// pre-smoothing e~ = Iter(A_i, f, start); r_{i+1} = U_i^T (f - A_i e~) (CG's recurrence
+// residual, or an explicit product); the coarser level is visited once (V: this is
+// Algorithm 1), twice (W), or F-then-V (F), each visit from the previous one's
+// result; e~ += V_i^T e_{i+1}; post-smoothing e = Iter(A_i, f, e~).
+static void cycle_visit(Matrix& M, const h2mg_solve_opts& o, int i, const double* f, bool from_zero, int kind,
+                        int nr, cudaStream_t s) {
   Work W = work(M);
   const bool f32 = o.precision == H2MG_PREC_MIXED_F32;
   const int l = M.lev;
-  if (l == 1) {
-    coarse_solve_multi(M, r1, W.et[1], nr, s);
+  if (i == l) {
+    coarse_solve_multi(M, f, W.et[l], nr, s);                        // e_l = dir_sol(A_l, r_l)
     return;
   }
-  auto iters = [&](int i) {
-    if (i == 1) return o.n_f;
-    return (o.skip_square_levels && square_level(M, i)) ? 0 : o.n_c;
-  };
-  const double* ri = r1;
-  for (int i = 1; i < l; ++i) {
-    const int ni = iters(i);
-    const int64_t N = level_size(M, i);
-    smooth_multi(M, i, f32, ri, nullptr, ni, W.et[i], W.cr, nr, s);   // e~_i = Iter(A_i, r_i, 0)
-    if (o.explicit_restrict_residual) {                              // r_i - A_i e~_i, explicitly
-      apply_level_multi(M, i, f32, W.et[i], N, W.cq, N, nr, s);
-      { k_sub<<<vec_grid(N * nr), 256, 0, s>>>(ri, W.cq, W.cr, N * nr); ::h2mg::count_launch(); }
-      H2_LAUNCH_CHECK();
-    }
-    restrict_multi(M, i, W.cr, W.r[i + 1], nr, s);                   // r_{i+1} = U_i^T (r_i - A_i e~_i)
-    ri = W.r[i + 1];
+  const int ni = (i == 1) ? o.n_f : ((o.skip_square_levels && square_level(M, i)) ? 0 : o.n_c);
+  const int64_t N = level_size(M, i);
+  smooth_multi(M, i, f32, f, from_zero ? nullptr : W.et[i], ni, W.et[i], W.cr, nr, s);   // e~_i = Iter(A_i, r_i, .)
+  if (o.explicit_restrict_residual) {                                // r_i - A_i e~_i, explicitly
+    apply_level_multi(M, i, f32, W.et[i], N, W.cq, N, nr, s);
+    { k_sub<<<vec_grid(N * nr), 256, 0, s>>>(f, W.cq, W.cr, N * nr); ::h2mg::count_launch(); }
+    H2_LAUNCH_CHECK();
   }
-  coarse_solve_multi(M, W.r[l], W.et[l], nr, s);                     // e_l = dir_sol(A_l, r_l)
-  for (int i = l - 1; i >= 1; --i) {
-    const int ni = iters(i);
-    prolong_add_multi(M, i, W.et[i + 1], W.et[i], nr, s);            // e~_i += V_i^T e_{i+1}
-    const double* fi = (i == 1) ? r1 : W.r[i];
-    smooth_multi(M, i, f32, fi, W.et[i], ni, W.et[i], nullptr, nr, s);   // e_i = Iter(A_i, r_i, e~_i)
-  }
+  restrict_multi(M, i, W.cr, W.r[i + 1], nr, s);                     // r_{i+1} = U_i^T (r_i - A_i e~_i)
+  const int kids[3][2] = {{H2MG_CYCLE_V, -1}, {H2MG_CYCLE_W, H2MG_CYCLE_W}, {H2MG_CYCLE_F, H2MG_CYCLE_V}};
+  for (int k = 0; k < 2 && kids[kind][k] >= 0; ++k) cycle_visit(M, o, i + 1, W.r[i + 1], k == 0, kids[kind][k], nr, s);
+  prolong_add_multi(M, i, W.et[i + 1], W.et[i], nr, s);              // e~_i += V_i^T e_{i+1}
+  smooth_multi(M, i, f32, f, W.et[i], ni, W.et[i], nullptr, nr, s);  // e_i = Iter(A_i, r_i, e~_i)
+}
+
+// e_1 of one multigrid cycle (o.cycle; the V-cycle is Algorithm 1) for nr columns of
+// r_1 (n x nr, leading dimension n), into the level-1 error buffer W.et[1]. No host
+// synchronisation and no allocation: the sequence can be captured into a CUDA graph.
+static void vcycle_core(Matrix& M, const h2mg_solve_opts& o, const double* r1, int nr, cudaStream_t s) {
+  H2_REQUIRE(nr >= 1 && nr <= NRMAX, H2MG_ERR_INVALID_ARG, "too many columns for one V-cycle");
+  H2_REQUIRE(o.cycle >= H2MG_CYCLE_V && o.cycle <= H2MG_CYCLE_F, H2MG_ERR_INVALID_ARG, "unknown cycle type");
+  cycle_visit(M, o, 1, r1, true, o.cycle, nr, s);
 }
 
 // One V-cycle for nr columns: x_out = x0 + e_1 given r1 = b - A x0 (x0, r1 and x_out
@@ -444,7 +457,7 @@ void vcycle(Matrix& M, const h2mg_solve_opts& o, const double* x0, const double*
 // setting and column count; replayed with one launch per outer iteration, or used as
 // one branch of a graph over several independent problems.
 struct GraphEntry {
-  int nr, n_f, n_c, f32, err, skip, prof;
+  int nr, n_f, n_c, f32, err, skip, prof, cyc;
   cudaGraph_t graph = nullptr;        // the captured sequence
   cudaGraphExec_t exec = nullptr;     // instantiated on first replay
   int64_t launches = 0;               // kernels per replay
@@ -472,10 +485,15 @@ void destroy_graphs(Matrix& M) {
   }
 }
 
-// Block products of one V-cycle, from above (event pairs of a profiled graph).
+// Block products of one cycle, from above (event pairs of a profiled graph): level i
+// is visited once per V-cycle, 2^(i-1) times per W-cycle and i times per F-cycle.
 static size_t products_bound(const Matrix& M, const h2mg_solve_opts& o, int nr) {
   size_t applies = 0;
-  for (int i = 1; i < M.lev; ++i) applies += 2 * (size_t)((i == 1) ? o.n_f : o.n_c) + 3;
+  for (int i = 1; i < M.lev; ++i) {
+    const size_t visits = o.cycle == H2MG_CYCLE_W ? ((size_t)1 << std::min(i - 1, 40))
+                          : o.cycle == H2MG_CYCLE_F ? (size_t)i : 1;
+    applies += visits * (2 * (size_t)((i == 1) ? o.n_f : o.n_c) + 3);
+  }
   return applies * 2 * (size_t)nr;   // at most two products per column group, nr groups
 }
 
@@ -487,12 +505,12 @@ static int vcycle_graph(Matrix& M, const h2mg_solve_opts& o, int nr, int prof) {
   for (size_t k = 0; k < M.graphs->g.size(); ++k) {
     const GraphEntry& e = M.graphs->g[k];
     if (e.nr == nr && e.n_f == o.n_f && e.n_c == o.n_c && e.f32 == f32 && e.err == o.explicit_restrict_residual &&
-        e.skip == o.skip_square_levels && e.prof == prof)
+        e.skip == o.skip_square_levels && e.prof == prof && e.cyc == o.cycle)
       return (int)k;
   }
   if (!M.cap_stream) H2_CUDA(cudaStreamCreateWithFlags(&M.cap_stream, cudaStreamNonBlocking));
   Work W = work(M);
-  GraphEntry e{nr, o.n_f, o.n_c, f32, o.explicit_restrict_residual, o.skip_square_levels, prof};
+  GraphEntry e{nr, o.n_f, o.n_c, f32, o.explicit_restrict_residual, o.skip_square_levels, prof, o.cycle};
   auto drop_events = [&](size_t from) {
     for (size_t k = from; k < e.ev.size(); ++k) best_effort(cudaEventDestroy(e.ev[k]), "cudaEventDestroy (graph)");
     e.ev.resize(std::min(from, e.ev.size()));
@@ -579,39 +597,51 @@ static void vcycle_solve_step(Matrix& M, const h2mg_solve_opts& o, int nr, cudaS
   if (e.prof) M.graphs->pending = k;
 }
 
-// x^T y on the device (two-pass deterministic sum), read back to the host.
+// out[c] = sum of the np partials of column c (blockIdx.x), in a fixed order.
+__global__ void __launch_bounds__(256) k_sum_parts(const double* __restrict__ part, int np,
+                                                   double* __restrict__ out) {
+  const double t = cta_sum_parts(part + blockIdx.x * NPART, np);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
+// Partials and result of h2mg_dot, per device: allocated on the first call on that
+// device and kept until the process exits (each call synchronises before returning,
+// so calls from one thread never overlap; a mutex serialises threads).
+static std::mutex g_dot_mu;
+static double* g_dot_ws[128] = {nullptr};
+
+// x^T y on the device (partials, then their fixed-order sum), read back to the host.
 double device_dot(const double* a, const double* b, int64_t n, cudaStream_t s) {
   if (n == 0) return 0.0;
-  double* part = nullptr;
-  H2_CUDA(cudaMalloc(&part, sizeof(double) * NPART));
+  int dev = 0;
+  H2_CUDA(cudaGetDevice(&dev));
+  H2_REQUIRE(dev >= 0 && dev < 128, H2MG_ERR_UNSUPPORTED, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_dot_mu);
+  if (!g_dot_ws[dev]) H2_CUDA(cudaMalloc(&g_dot_ws[dev], sizeof(double) * (NPART + 32)));
+  double* part = g_dot_ws[dev];
+  dot_part(a, b, n, n, 1, part, s);
+  { k_sum_parts<<<1, 256, 0, s>>>(part, part_grid(n), part + NPART); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
   double t = 0.0;
-  try {
-    dot_part(a, b, n, n, 1, part, s);
-    std::vector<double> h(part_grid(n));
-    H2_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
-    H2_CUDA(cudaStreamSynchronize(s));
-    for (double v : h) t += v;
-  } catch (...) {
-    cudaFree(part);
-    throw;
-  }
-  cudaFree(part);
+  H2_CUDA(cudaMemcpyAsync(&t, part + NPART, sizeof(double), cudaMemcpyDeviceToHost, s));
+  H2_CUDA(cudaStreamSynchronize(s));
   return t;
 }
 
-// out[c] = a_c^T b_c for nr columns of length n (leading dimension n), on the host.
+// out[c] = a_c^T b_c for nr columns of length n (leading dimension n): partials and
+// their sums on the device, the nr results read back.
 static void dots_host(Matrix& M, const double* a, const double* b, int64_t n, int nr, double* out, cudaStream_t s) {
   Work W = work(M);
   dot_part(a, b, n, n, nr, W.pa, s);
-  const int np = part_grid(n);
-  std::vector<double> h((size_t)NPART * nr);
-  H2_CUDA(cudaMemcpyAsync(h.data(), W.pa, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  { k_sum_parts<<<nr, 256, 0, s>>>(W.pa, part_grid(n), W.scal + 4 * NRMAX); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
+  H2_CUDA(cudaMemcpyAsync(out, W.scal + 4 * NRMAX, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
   H2_CUDA(cudaStreamSynchronize(s));
-  for (int c = 0; c < nr; ++c) {
-    double t = 0.0;
-    for (int i = 0; i < np; ++i) t += h[(size_t)c * NPART + i];
-    out[c] = t;
-  }
+}
+
+// The same, for callers outside this file.
+void dots(Matrix& M, const double* a, const double* b, int64_t n, int nr, double* out, cudaStream_t s) {
+  dots_host(M, a, b, n, nr, out, s);
 }
 
 // y_c += alpha[c] x_c with the coefficients from the host.
@@ -623,6 +653,95 @@ static void axpy_cols(Matrix& M, const double* alpha, const double* x, double* y
   H2_LAUNCH_CHECK();
 }
 
+// y_c = x_c + beta[c] y_c with the coefficients from the host.
+static void xpby_cols(Matrix& M, const double* beta, const double* x, double* y, int64_t n, int nr, cudaStream_t s) {
+  Work W = work(M);
+  H2_CUDA(cudaMemcpyAsync(W.scal + NRMAX, beta, sizeof(double) * nr, cudaMemcpyHostToDevice, s));
+  { k_xpby_cols<<<dim3(vec_grid(n), nr), 256, 0, s>>>(W.scal + NRMAX, x, y, n, n); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
+}
+
+// Unpreconditioned CG on A x = b for nr columns, the comparison solver of the paper's
+// experiments (Sec. 4): q = A p, alpha = rho / p^T q, x += alpha p, r -= alpha q,
+// rho' = r^T r, p = r + (rho'/rho) p, from x's initial guess (r = b - A x). A column
+// stops when its recurrence residual |r| / |b| <= tol (or at a breakdown p^T A p <= 0);
+// info.cycles counts CG iterations (one product of the primary copy each) and
+// info.relres is the explicitly recomputed float64 residual.
+static h2mg_status solve_cg_multi(Matrix& M, const double* b, double* x, int nr, const h2mg_solve_opts& o,
+                                  h2mg_solve_info* info, cudaStream_t s) {
+  Work W = work(M);
+  const int64_t n = M.n;
+  auto t0 = std::chrono::steady_clock::now();
+  double nb[NRMAX], rho[NRMAX], rn[NRMAX], pq[NRMAX], al[NRMAX], be[NRMAX];
+  bool done[NRMAX], conv[NRMAX];
+  double* r = W.t1;
+  double* p = (double*)M.wfcg.p;
+  double* q = p + n * NRMAX;
+  dots_host(M, b, b, n, nr, nb, s);
+  for (int c = 0; c < nr; ++c) {
+    H2_REQUIRE(std::isfinite(nb[c]), H2MG_ERR_NAN, "right-hand side is not finite");
+    nb[c] = std::sqrt(nb[c]);
+    done[c] = conv[c] = false;
+    info[c] = h2mg_solve_info{};
+  }
+  apply_level_multi(M, 1, false, x, n, W.t2, n, nr, s);
+  { k_sub<<<vec_grid(n * nr), 256, 0, s>>>(b, W.t2, r, n * nr); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
+  H2_CUDA(cudaMemcpyAsync(p, r, sizeof(double) * n * nr, cudaMemcpyDeviceToDevice, s));
+  dots_host(M, r, r, n, nr, rho, s);
+  bool nan = false;
+  for (int it = 0; it <= o.max_cycles; ++it) {
+    bool all = true;
+    for (int c = 0; c < nr; ++c) {
+      if (done[c]) continue;
+      const double rel = nb[c] > 0 ? std::sqrt(rho[c]) / nb[c] : 0.0;
+      if (it < 256) info[c].relres_hist[it] = rel;
+      info[c].cycles = it;
+      if (!std::isfinite(rel)) {
+        nan = true;
+        done[c] = true;
+      } else if (rel <= o.tol) {
+        conv[c] = true;
+        done[c] = true;
+      }
+      all = all && done[c];
+    }
+    if (all || nan || it == o.max_cycles) break;
+    apply_level_multi(M, 1, false, p, n, q, n, nr, s);
+    dots_host(M, p, q, n, nr, pq, s);
+    for (int c = 0; c < nr; ++c) {
+      if (!done[c] && !(pq[c] > 0.0)) done[c] = true;   // breakdown: stop this column
+      al[c] = done[c] ? 0.0 : rho[c] / pq[c];
+    }
+    axpy_cols(M, al, p, x, n, nr, s);                         // x += alpha p
+    for (int c = 0; c < nr; ++c) al[c] = -al[c];
+    axpy_cols(M, al, q, r, n, nr, s);                         // r -= alpha q
+    dots_host(M, r, r, n, nr, rn, s);
+    for (int c = 0; c < nr; ++c) {
+      be[c] = done[c] ? 0.0 : rn[c] / rho[c];
+      if (!done[c]) rho[c] = rn[c];
+    }
+    xpby_cols(M, be, r, p, n, nr, s);                         // p = r + beta p
+  }
+  // the explicit float64 residual of the result
+  apply_level_multi(M, 1, false, x, n, W.t2, n, nr, s);
+  { k_sub<<<vec_grid(n * nr), 256, 0, s>>>(b, W.t2, r, n * nr); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
+  double rr[NRMAX];
+  dots_host(M, r, r, n, nr, rr, s);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h2mg_status st = H2MG_OK;
+  for (int c = 0; c < nr; ++c) {
+    info[c].relres = nb[c] > 0 ? std::sqrt(rr[c]) / nb[c] : 0.0;
+    info[c].converged = conv[c] ? 1 : 0;
+    info[c].ms_solve = ms;
+    if (!conv[c]) st = H2MG_ERR_NOT_CONVERGED;
+    if (!std::isfinite(info[c].relres)) nan = true;
+  }
+  if (nan) st = H2MG_ERR_NAN;
+  return st;
+}
+
 // Outer iteration for nr columns (b, x: n x nr, leading dimension n): repeated
 // V-cycles x <- x + V(b - A x) (Sec. 3.3), or flexible CG preconditioned by one
 // V-cycle (each new direction is made A-orthogonal to the previous one because the
@@ -632,6 +751,7 @@ static void axpy_cols(Matrix& M, const double* alpha, const double* x, double* y
 h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2mg_solve_opts& o,
                         h2mg_solve_info* info, cudaStream_t s) {
   H2_REQUIRE(nr >= 1 && nr <= NRMAX, H2MG_ERR_INVALID_ARG, "too many columns for one solve");
+  if (o.outer == H2MG_OUTER_CG) return solve_cg_multi(M, b, x, nr, o, info, s);
   Work W = work(M);
   const int64_t n = M.n;
   auto t0 = std::chrono::steady_clock::now();
@@ -732,16 +852,13 @@ static void dots_many(const std::vector<Matrix*>& Ms, const std::vector<const do
     if (!want[p]) continue;
     Work W = work(*Ms[p]);
     dot_part(a[p], b[p], Ms[p]->n, Ms[p]->n, 1, W.pa, s);
-    H2_CUDA(cudaMemcpyAsync(hp.h + p * NPART, W.pa, sizeof(double) * part_grid(Ms[p]->n), cudaMemcpyDeviceToHost,
-                            s));
+    { k_sum_parts<<<1, 256, 0, s>>>(W.pa, part_grid(Ms[p]->n), W.scal + 4 * NRMAX); ::h2mg::count_launch(); }
+    H2_LAUNCH_CHECK();
+    H2_CUDA(cudaMemcpyAsync(hp.h + p, W.scal + 4 * NRMAX, sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   H2_CUDA(cudaStreamSynchronize(s));
-  for (size_t p = 0; p < P; ++p) {
-    if (!want[p]) continue;
-    double t = 0.0;
-    for (int i = 0; i < part_grid(Ms[p]->n); ++i) t += hp.h[p * NPART + i];
-    out[p] = t;
-  }
+  for (size_t p = 0; p < P; ++p)
+    if (want[p]) out[p] = hp.h[p];
 }
 
 // One graph whose branches are the captured V-cycles of the problems in `sel`:

@@ -57,6 +57,10 @@ def test_build_rejects_bad_arguments_without_cuda(lib):
         (pts.ctypes.data, 100, 2, pkg._Kernel(0, -0.1, 0.0, 2, None, None), good),  # length
         (pts.ctypes.data, 100, 2, pkg._Kernel(3, 1.0, 0.0, 2, None, None), good),   # single layer without areas or diagonal
         (pts.ctypes.data, 100, 2, pkg._Kernel(9, 1.0, 0.0, 2, None, None), good),   # kind
+        (pts.ctypes.data, 100, 2, k, pkg._BuildOpts(32, 3, 1.0, 0, 0, -1, 2, 1e-9, 64)),   # basis kind
+        (pts.ctypes.data, 100, 2, k, pkg._BuildOpts(32, 3, 1.0, 0, 0, -1, 1, 1e-9, 0)),    # skeleton rank 0
+        (pts.ctypes.data, 100, 2, k, pkg._BuildOpts(32, 3, 1.0, 0, 0, -1, 1, 1e-9, 65)),   # skeleton rank > 64
+        (pts.ctypes.data, 100, 2, k, pkg._BuildOpts(32, 3, 1.0, 0, 0, -1, 1, -1.0, 64)),   # negative tolerance
     ]
     for (p, n, d, kk, o) in cases:
         st = lib.h2mg_build(p, n, d, ctypes.byref(kk), ctypes.byref(o), None, ctypes.byref(h))
@@ -72,6 +76,7 @@ def test_null_handles(lib):
     assert lib.h2mg_apply(None, None, None, 1, 1, None) == 1
     assert lib.h2mg_apply_noalloc(None, None, None, None) == 1
     assert lib.h2mg_profile(None, 1, None, None, None) == 1
+    assert lib.h2mg_autotune(None, None, None, 0, None) == 1
     out = ctypes.c_double()
     assert lib.h2mg_dot(None, None, 4, ctypes.byref(out), None) == 1
     import paper_2501_17656_gb300 as pkg
@@ -93,3 +98,18 @@ def test_batched_solve_rejects_bad_arguments_without_cuda(lib):
     assert lib.h2mg_solve_batched(2, nul, nul, nul, ctypes.byref(bad), infos, None) == 1
     assert lib.h2mg_last_error().decode()
 
+
+
+def test_solve_rejects_bad_outer_and_cycle_without_cuda(lib):
+    """An unknown outer loop or cycle type is refused (here with a null handle the
+    handle check comes first; the batched solve checks its options before the
+    handles)."""
+    import paper_2501_17656_gb300 as pkg
+    infos = (pkg.SolveInfo * 2)()
+    arr = ctypes.c_void_p * 2
+    nul = arr(None, None)
+    for field, val in (("outer", 2), ("outer", 9), ("cycle", 3), ("cycle", -1)):
+        o = pkg.H2Matrix._opts()
+        setattr(o, field, val)
+        assert lib.h2mg_solve_batched(2, nul, nul, nul, ctypes.byref(o), infos, None) == 1
+        assert lib.h2mg_last_error().decode()

@@ -1,12 +1,16 @@
 """Full-size checks at the bench workload's size (2^20 points in the unit cube,
-Gaussian kernel, leaf 64, 4x4x4 nodes, eta 1), in the precisions the bench runs.
+Gaussian kernel exp(-r^2/0.05^2) + 1e-3 I, leaf 64, eta 1, bases skeletonized to
+1e-9 with rank <= 64), in the precisions the bench runs.
 
 The oracle cannot build this matrix on the host in test time, so these tests use
-properties that hold at any size, each derived from the paper's construction:
+what it can compute one by one -- rows of the exact kernel matrix by its formula --
+and properties that hold at any size, each derived from the paper's construction:
 symmetry of every level operator (V_i = U_i^T), the Galerkin identity
 A_{i+1} = U_i^T A_i U_i with orthonormal transfers (Sec. 3.3, eq. a2_str), the
 coarse solve against its own operator, and -- for a kernel that Chebyshev
-interpolation reproduces exactly -- sampled rows computed by brute force.
+interpolation reproduces exactly -- sampled rows computed by brute force. One more
+test reproduces the finding that the 4x4x4-node Chebyshev form of this matrix is not
+positive definite: plain CG in float64 meets a direction with p^T A p < 0.
 """
 import numpy as np
 import pytest
@@ -40,11 +44,43 @@ def test_polynomial_kernel_rows_full_size():
     torch.cuda.empty_cache()
 
 
+def test_chebyshev_form_is_indefinite_at_full_size():
+    """4x4x4 Chebyshev nodes, eta 1, leaf 64 at 2^20 points: plain CG in float64 on
+    A x = b meets p^T A p < 0 within 400 iterations, and the product of that direction,
+    recomputed, stays negative: the form is not positive definite (its interpolation
+    error exceeds the nugget), so no H2-MG or CG solve of it can be expected to converge."""
+    p = W.workload(2)
+    C = pkg.H2Matrix(torch.from_numpy(p["points"]).cuda(), "gaussian", length=0.05, nugget=1e-3, leaf=64, q=4,
+                     eta=1.0, storage="f64")
+    b = torch.from_numpy(p["b"]).cuda()
+    r = b.clone()
+    d = r.clone()
+    rho = float(r @ r)
+    found = None
+    for it in range(400):
+        q = C.apply(d)
+        pq = float(d @ q)
+        if pq <= 0:
+            v = d / d.norm()
+            found = (it, float(v @ C.apply(v)))
+            break
+        al = rho / pq
+        r -= al * q
+        rn = float(r @ r)
+        d = r + (rn / rho) * d
+        rho = rn
+    C.close()
+    del C
+    torch.cuda.empty_cache()
+    assert found is not None and found[1] < 0, found
+
+
 @pytest.fixture(scope="module")
 def big():
     p = W.workload(2)
     A = pkg.H2Matrix(torch.from_numpy(p["points"]).cuda(), "gaussian", length=0.05, nugget=1e-3,
-                     leaf=64, q=4, eta=1.0, storage="f64", with_f32=True)
+                     leaf=64, eta=1.0, storage="f64", with_f32=True, basis="skeleton", basis_tol=1e-9,
+                     rank_max=64)
     yield A
     A.close()
     torch.cuda.empty_cache()
@@ -55,11 +91,37 @@ def rnd(n, seed):
     return torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
 
 
+def rnd_level(A, i, seed):
+    """A random level-i vector with zeros in the padded slots beyond each rank."""
+    v = rnd(A.level_size(i), seed)
+    if i >= 2:
+        KC = A.query("KC")
+        rk = A.export("RANKS", A.query("L") - i + 2)
+        mask = (np.arange(KC)[None, :] < rk[:, None]).ravel()
+        v[torch.from_numpy(~mask).cuda()] = 0.0
+    return v
+
+
+def test_sampled_rows_against_the_exact_kernel(big):
+    """256 sampled rows of A x against the same rows of the exact kernel matrix (the
+    oracle's formula): the relative error is the compression error, about the basis
+    tolerance, in float64 and within FP32 rounding in the FP32 copy."""
+    from oracle.kernels import kernel_rows
+    p = W.workload(2)
+    x = np.random.default_rng(1).standard_normal(N)
+    rows = np.random.default_rng(2).choice(N, 256, replace=False)
+    yr = kernel_rows("gaussian", p["points"], rows, 0.05, 1e-3) @ x
+    for prec, bound in (("f64", 1e-7), ("mixed_f32", 1e-5)):
+        y = big.apply_level(1, torch.from_numpy(x).cuda(), prec).cpu().numpy()
+        err = np.linalg.norm(y[rows] - yr) / np.linalg.norm(yr)
+        assert err < bound, (prec, err)
+
+
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("mixed_f32", 2e-6)])
 def test_every_level_is_symmetric(big, prec, tol):
     for i in range(1, big.levels + 1):
         n = big.level_size(i)
-        x, y = rnd(n, 2 * i), rnd(n, 2 * i + 1)
+        x, y = rnd_level(big, i, 2 * i), rnd_level(big, i, 2 * i + 1)
         a = float(y @ big.apply_level(i, x, prec))
         b = float(x @ big.apply_level(i, y, prec))
         scale = float(x.norm() * big.apply_level(i, y, prec).norm())
@@ -68,7 +130,7 @@ def test_every_level_is_symmetric(big, prec, tol):
 
 def test_galerkin_identity_every_level(big):
     for i in range(1, big.levels):
-        v = rnd(big.level_size(i + 1), 100 + i)
+        v = rnd_level(big, i + 1, 100 + i)
         u = big.prolong(i, v)
         assert abs(float(u.norm()) - float(v.norm())) <= 1e-12 * float(v.norm())   # orthonormal U_i
         assert float((big.restrict(i, u) - v).norm()) <= 1e-12 * float(v.norm())
@@ -79,7 +141,7 @@ def test_galerkin_identity_every_level(big):
 
 def test_coarse_solve_inverts_coarse_operator(big):
     l = big.levels
-    r = rnd(big.level_size(l), 7)
+    r = rnd_level(big, l, 7)
     e = big.coarse_solve(r)
     res = float((big.apply_level(l, e) - r).norm() / r.norm())
     assert res < 1e-8, res

@@ -98,3 +98,57 @@ def test_adjoint_gradients_near_dense_autograd(data):
     assert abs(gl - lt.grad.item()) <= 1e-2 * abs(lt.grad.item())
     assert abs(gs - st.grad.item()) <= 1e-2 * abs(st.grad.item())
     assert np.linalg.norm(gb - bt.grad.cpu().numpy()) <= 1e-2 * np.linalg.norm(gb)
+
+
+def test_skeleton_gradients_match_dense_autograd_closely(data):
+    """With bases skeletonized to 1e-9 the H2 loss is within the compression error of
+    the exact one, so the adjoint gradients agree with dense float64 autograd to about
+    1e-6 instead of the 1e-2 of the 4x4x4-node interpolation, and central differences of
+    the rebuilt loss (step 1e-6, solves to 1e-13) match them to 1e-6."""
+    X, y, b = data
+    kw = dict(tol=1e-13, basis="skeleton", basis_tol=1e-10)
+    Xd = torch.from_numpy(X).cuda()
+    yt, bt, lt, st = cuda(y, True), cuda(b, True), cuda(L_, True), cuda(S_, True)
+    L = pkg.MaternLoss.apply(Xd, yt, bt, lt, st, **kw)
+    L.backward()
+    Xt = torch.tensor(X, dtype=torch.float64, device="cuda")
+    l2, s2, y2, b2 = cuda(L_, True), cuda(S_, True), cuda(y, True), cuda(b, True)
+    u = math.sqrt(3.0) * torch.cdist(Xt, Xt) / l2
+    K = (1 + u) * torch.exp(-u) + s2 * torch.eye(N, dtype=torch.float64, device="cuda")
+    Lt = 0.5 * y2 @ torch.linalg.solve(K, y2) + torch.linalg.solve(K, b2).sum()
+    Lt.backward()
+    assert abs(L.item() - Lt.item()) <= 1e-7 * abs(Lt.item())
+    assert abs(lt.grad.item() - l2.grad.item()) <= 1e-6 * abs(l2.grad.item())
+    assert abs(st.grad.item() - s2.grad.item()) <= 1e-6 * abs(s2.grad.item())
+    assert np.linalg.norm((bt.grad - b2.grad).cpu().numpy()) <= 1e-6 * np.linalg.norm(b2.grad.cpu().numpy())
+
+    def loss(l, s):
+        with torch.no_grad():
+            return pkg.MaternLoss.apply(Xd, cuda(y), cuda(b), cuda(l), cuda(s), **kw).item()
+
+    h = 1e-6
+    fd_l = (loss(L_ * (1 + h), S_) - loss(L_ * (1 - h), S_)) / (2 * h * L_)
+    fd_s = (loss(L_, S_ * (1 + h)) - loss(L_, S_ * (1 - h))) / (2 * h * S_)
+    assert abs(lt.grad.item() - fd_l) <= 1e-6 * abs(fd_l), (lt.grad.item(), fd_l)
+    assert abs(st.grad.item() - fd_s) <= 1e-6 * abs(fd_s), (st.grad.item(), fd_s)
+
+
+def test_loss_call_rejects_a_foreign_derivative_matrix(data):
+    X, y, b = data
+    Xd = torch.from_numpy(X).cuda()
+    K = pkg.H2Matrix(Xd, "matern32", length=L_, nugget=S_, leaf=64, q=4)
+    G = pkg.H2Matrix(Xd, "gaussian", length=L_, nugget=S_, leaf=64, q=4)
+    dG = G.sibling("dmatern32_dl", length=L_)
+    o = pkg.H2Matrix._opts(tol=1e-10)
+    loss, dl = pkg.ctypes.c_double(), pkg.ctypes.c_double()
+    yy, bb = cuda(y), cuda(b)
+    st = K._lib.h2mg_matern_loss_grad(K._h, dG._h, pkg._ptr(yy), pkg._ptr(bb), pkg.ctypes.byref(o),
+                                      pkg.ctypes.byref(loss), None, None, pkg.ctypes.byref(dl), None, None,
+                                      pkg._stream())
+    assert st == 1          # dK is not K's sibling
+    st = G._lib.h2mg_matern_loss_grad(G._h, None, pkg._ptr(yy), pkg._ptr(bb), pkg.ctypes.byref(o),
+                                      pkg.ctypes.byref(loss), None, None, None, None, None, pkg._stream())
+    assert st == 1          # not a Matern matrix
+    dG.close()
+    G.close()
+    K.close()

@@ -1,0 +1,176 @@
+"""GPU parity of the skeleton bases (recursive skeletonization to a tolerance, the
+tolerance-driven construction of the paper's matrices, Sec. 4.1) through the C ABI.
+
+Expected values come from ``oracle/`` only. The skeletons are integer decisions
+taken by a column-pivoted QR in float64 on both sides (same greedy rule and tie
+band), so ranks and skeleton points must agree exactly; the operators built on them
+must then agree to 1e-12 like the Chebyshev ones. Solves at the density of the
+2^20-point workload (where the Chebyshev form is indefinite) converge, and their
+cycle counts agree with the oracle's within one: with two levels the V-cycle is one
+CG step and an exact coarse solve, so rounding order barely moves it.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import H2MG, H2Matrix, KernelSpec, SolveOpts, solve, solve_fcg, solve_mixed, surface_diag
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2501_17656_gb300 as pkg  # noqa: E402
+
+pkg.load_library(build_if_missing=True)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def c2_density(n):
+    """n points at the density of 2^20 uniform points in the unit cube."""
+    return W.uniform_points(n, 3, 2) * (n / 2.0 ** 20) ** (1 / 3)
+
+
+CASES = {
+    "exp2d": lambda: (W.workload(1, n=2048)["points"], dict(kind="exponential", length=0.1, nugget=1e-2, leaf=64),
+                      1e-8, 64),
+    "gauss3d_c2_density": lambda: (c2_density(4096), dict(kind="gaussian", length=0.05, nugget=1e-3, leaf=64),
+                                   1e-9, 64),
+    "gauss2d_ragged_cap24": lambda: (W.uniform_points(1500, 2, 8), dict(kind="gaussian", length=0.2, nugget=1e-3,
+                                                                        leaf=32), 1e-7, 24),
+    "poly3d_exact_rank": lambda: (W.uniform_points(1500, 3, 3), dict(kind="poly", degree=2, nugget=1.0, leaf=32),
+                                  1e-11, 64),
+    "matern1d": lambda: (W.uniform_points(3001, 1, 9), dict(kind="matern32", length=0.05, nugget=1e-2, leaf=16),
+                         1e-10, 16),
+}
+
+
+def build_pair(X, kw, tol, rmax, weights=None, diag=None, with_f32=False):
+    A = pkg.H2Matrix(cuda(X), kw["kind"], length=kw.get("length", 1.0), nugget=kw.get("nugget", 0.0),
+                     degree=kw.get("degree", 2), weights=None if weights is None else cuda(weights),
+                     diag=None if diag is None else cuda(diag), leaf=kw["leaf"], eta=kw.get("eta", 1.0),
+                     basis="skeleton", basis_tol=tol, rank_max=rmax, with_f32=with_f32)
+    ks = KernelSpec(kw["kind"], kw.get("length", 1.0), kw.get("nugget", 0.0), kw.get("degree", 2), weights, diag)
+    h = H2Matrix(X, ks, kw["leaf"], 4, kw.get("eta", 1.0), basis="skeleton", tol=tol, rank_max=rmax)
+    return A, h
+
+
+def pad(mg, i, v, KC):
+    """oracle level-i coefficients (ranks vary by cluster) -> the library's layout
+    (KC slots per cluster, zeros beyond the rank)"""
+    off = mg.h.coef_offsets(mg.m(i))
+    out = np.zeros((1 << mg.m(i)) * KC)
+    for j in range(1 << mg.m(i)):
+        out[j * KC: j * KC + off[j + 1] - off[j]] = v[off[j]:off[j + 1]]
+    return out
+
+
+def unpad(mg, i, v, KC):
+    off = mg.h.coef_offsets(mg.m(i))
+    return np.concatenate([v[j * KC: j * KC + off[j + 1] - off[j]] for j in range(1 << mg.m(i))])
+
+
+def check_structure(A, h):
+    """Ranks and skeletons of every level identical (original point indices)."""
+    perm = h.tree.perm
+    assert A.query("TSTAR") == h.tstar and A.query("L") == h.L
+    for ell in range(h.tstar, h.L + 1):
+        rk = A.export("RANKS", ell)
+        np.testing.assert_array_equal(rk, [h.rank[(ell, j)] for j in range(1 << ell)])
+        sk = A.export("SKELETON", ell).reshape(1 << ell, 64)
+        for j in range(1 << ell):
+            want = perm[h.skeletons.skel[(ell, j)]]
+            got = sk[j][: len(want)]
+            assert (sk[j][len(want):] == -1).all()
+            np.testing.assert_array_equal(got, want, err_msg=f"level {ell} cluster {j}")
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_skeletons_and_operators_match_the_oracle(name):
+    X, kw, tol, rmax = CASES[name]()
+    A, h = build_pair(X, kw, tol, rmax)
+    check_structure(A, h)
+    x = np.random.default_rng(11).standard_normal(X.shape[0])
+    assert rel(A.apply(cuda(x)).cpu().numpy(), h.apply(x)) < 1e-12
+    mg = H2MG(h)
+    assert A.levels == mg.l
+    KC = A.query("KC")
+    # The coarse operators depend on the bases themselves, and an interpolation matrix
+    # T = R11^{-1} R12 carries rounding of order cond(R11) * eps, with cond(R11) up to
+    # 1 / tol: two correct implementations differ there by about eps / tol. What is
+    # unique is the represented matrix: each GPU A_i must be the Galerkin product
+    # C_i^T A_1 C_i of the oracle's A_1 with the GPU's own prolongations C_i.
+    A1 = np.empty((X.shape[0], X.shape[0]))
+    A1[np.ix_(h.tree.perm, h.tree.perm)] = h.dense_blocks()
+    C = np.eye(X.shape[0])
+    for i in range(2, mg.l + 1):
+        assert A.level_size(i) == (1 << mg.m(i)) * KC
+        ni = A.level_size(i)
+        P = np.stack([A.prolong(i - 1, cuda(e)).cpu().numpy() for e in np.eye(ni)], axis=1)
+        C = C @ P
+        v = np.random.default_rng(i).standard_normal(ni)
+        keep = np.concatenate([np.arange(j * KC, j * KC + r) for j, r in enumerate(A.export("RANKS", mg.m(i)))])
+        v[np.setdiff1d(np.arange(ni), keep)] = 0.0          # padded slots hold zeros
+        y = A.apply_level(i, cuda(v)).cpu().numpy()
+        assert rel(y, C.T @ (A1 @ (C @ v))) < 1e-12, i
+        yo = unpad(mg, i, y, KC)
+        assert rel(yo, mg.apply(i, unpad(mg, i, v, KC))) < max(1e-12, 1e-14 / tol), i
+    A.close()
+
+
+def test_weighted_surface_kernel_skeletons():
+    """Panel areas as weights enter the sampled rows and the couplings."""
+    c, a, _ = W.perturbed_icosphere(12, 1)
+    A, h = build_pair(c, dict(kind="laplace_sl", leaf=32), 1e-9, 64, weights=a, diag=surface_diag(a))
+    check_structure(A, h)
+    x = np.random.default_rng(2).standard_normal(c.shape[0])
+    assert rel(A.apply(cuda(x)).cpu().numpy(), h.apply(x)) < 1e-12
+    A.close()
+
+
+@pytest.fixture(scope="module")
+def c2_pair():
+    X = c2_density(4096)
+    A, h = build_pair(X, dict(kind="gaussian", length=0.05, nugget=1e-3, leaf=64), 1e-9, 64, with_f32=True)
+    yield A, h, H2MG(h), W.normal_rhs(4096, 2)
+    A.close()
+
+
+@pytest.mark.parametrize("outer", ["vcycle", "fcg"])
+def test_solve_at_the_full_size_density_matches_cycle_count(c2_pair, outer):
+    """4096 points at the 2^20-point density: the GPU float64 solve converges to 1e-10
+    in the oracle's number of cycles +-1, the mixed-precision one (FP32 V-cycle) within
+    +-2 of the oracle's FP32-rounded run, and both float64 residuals are checked by the
+    oracle's product."""
+    A, h, mg, b = c2_pair
+    check_structure(A, h)
+    opts = SolveOpts(tol=1e-10, max_cycles=100)
+    if outer == "vcycle":
+        xo, io = solve(mg, b, opts)
+        xm, im = solve_mixed(mg, b, opts, low=np.float32)
+    else:
+        xo, io = solve_fcg(mg, b, opts)
+        xm, im = solve_fcg(mg, b, opts, low=np.float32)
+    assert io.converged and im.converged
+    for prec, ref, band in (("f64", io, 1), ("mixed_f32", im, 2)):
+        xg, ig = A.solve(cuda(b), tol=1e-10, max_cycles=100, outer=outer, precision=prec, use_graph=True)
+        assert ig.converged
+        assert abs(ig.cycles - ref.cycles) <= band, (prec, ig.cycles, ref.cycles)
+        r = b - h.apply(xg.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10 * 1.0001
+
+
+def test_bad_skeleton_options_are_rejected():
+    X = W.uniform_points(300, 2, 1)
+    for kw in (dict(rank_max=0), dict(rank_max=65), dict(basis_tol=-1.0), dict(basis_tol=float("nan"))):
+        with pytest.raises(pkg.H2MGError) as e:
+            pkg.H2Matrix(cuda(X), "gaussian", length=0.1, leaf=32, basis="skeleton", **kw)
+        assert e.value.name == "INVALID_ARG"

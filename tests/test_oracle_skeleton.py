@@ -213,3 +213,18 @@ def test_skeleton_solve_converges_like_the_dense_system():
     x, info = solve_fcg(mg, p["b"], SolveOpts(tol=1e-10, max_cycles=200))
     assert info.converged, info.history[-3:]
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-10 * kappa
+
+
+def test_kernel_rows_are_rows_of_the_dense_matrix():
+    """Sampled rows by the formula equal the rows of the dense matrix (both routes of
+    kernels.py), with weights and a diagonal override, and the nugget on the diagonal."""
+    from oracle.kernels import kernel_rows
+    c, a, _ = W.perturbed_icosphere(6, 0)
+    from oracle.kernels import surface_diag
+    K = dense_kernel_matrix("laplace_sl", c, weights=a, diag=surface_diag(a), nugget=0.1)
+    rows = [0, 5, 17, len(a) - 1]
+    np.testing.assert_array_equal(kernel_rows("laplace_sl", c, rows, weights=a, diag=surface_diag(a), nugget=0.1),
+                                  K[rows])
+    X = W.uniform_points(500, 3, 1)
+    K = dense_kernel_matrix("gaussian", X, 0.1, 1e-3)
+    np.testing.assert_allclose(kernel_rows("gaussian", X, [3, 499], 0.1, 1e-3), K[[3, 499]], rtol=1e-15, atol=0)

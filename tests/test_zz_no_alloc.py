@@ -1,5 +1,6 @@
 """h2mg_apply_noalloc: the H2 matrix-vector product for callers that cannot
-allocate device memory (stream capture, allocator callbacks, fully reserved memory).
+allocate device memory (allocator callbacks, memory reserved in full by another
+allocator).
 
 Its output must match h2mg_apply's within the matvec tolerance used elsewhere
 (1e-12 relative) on two calls in a row (the fixed scratch array keeps the first
@@ -58,7 +59,10 @@ def test_noalloc_rejects_host_vectors_and_oversized_problems():
         A.apply_noalloc(xh, np.empty_like(xh))
     assert e.value.name == "INVALID_ARG"
     A.close()
-    n = 1 << 19   # about 64 bytes of workspace per point: above the fixed 16 MiB
+    # 2-D, 3 x 3 nodes (KC = 16), leaf 32 at 2^19 points: 2^14 leaves and about 2^15
+    # clusters, so three 4 MiB coefficient buffers and two 4 MiB point buffers,
+    # about 20 MiB in all: above the fixed 16 MiB
+    n = 1 << 19
     X = torch.from_numpy(W.uniform_points(n, 2, 2)).cuda()
     B = pkg.H2Matrix(X, "exponential", length=0.1, nugget=1e-2, leaf=32, q=3, eta=1.0)
     x = torch.ones(n, dtype=torch.float64, device="cuda")
@@ -67,3 +71,23 @@ def test_noalloc_rejects_host_vectors_and_oversized_problems():
     assert e.value.name == "UNSUPPORTED"
     assert "bytes of scratch" in str(e.value)
     B.close()
+
+
+def test_noalloc_rejects_wrong_lengths_before_the_library():
+    """The library cannot see buffer sizes: a short x or y would be read or written
+    past its end on the device, so the binding rejects them first."""
+    p = W.workload(1, n=2048)
+    A = pkg.H2Matrix(torch.from_numpy(p["points"]).cuda(), "exponential", length=0.1, nugget=1e-2,
+                     leaf=64, q=4, eta=1.0)
+    x = torch.ones(2048, dtype=torch.float64, device="cuda")
+    for xx, yy in ((x[:2047], torch.empty_like(x)), (x, torch.empty(2047, dtype=torch.float64, device="cuda")),
+                   (x, torch.empty((2048, 2), dtype=torch.float64, device="cuda"))):
+        with pytest.raises(ValueError):
+            A.apply_noalloc(xx, yy)
+        with pytest.raises(ValueError):
+            A.apply(xx, yy)
+    y = torch.empty_like(x)
+    A.apply_noalloc(x, y)           # a well-formed call still works afterwards
+    ref = A.apply(x)
+    assert float((y - ref).norm() / ref.norm()) < 1e-12
+    A.close()

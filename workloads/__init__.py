@@ -34,6 +34,7 @@ import numpy as np
 __all__ = [
     "WORKLOADS",
     "uniform_points",
+    "tensor_grid",
     "normal_rhs",
     "perturbed_icosphere",
     "surface_problem_sizes",
@@ -48,6 +49,15 @@ def uniform_points(n: int, dim: int, k: int) -> np.ndarray:
     """
     rng = np.random.default_rng(1000 + k)
     return np.ascontiguousarray(rng.random((n, dim)))
+
+
+def tensor_grid(m: int) -> np.ndarray:
+    """The uniform m x m tensor grid on the unit square (the paper's 2-D workloads,
+    Sec. 4.1-4.2): points (i/(m-1), j/(m-1)), i, j = 0..m-1, the first coordinate
+    slowest. Shape (m*m, 2), float64."""
+    t = np.arange(m, dtype=np.float64) / max(m - 1, 1)
+    X, Y = np.meshgrid(t, t, indexing="ij")
+    return np.ascontiguousarray(np.stack([X.ravel(), Y.ravel()], axis=1))
 
 
 def normal_rhs(n: int, k: int, nrhs: int = 1) -> np.ndarray:
