@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1 << 20, help="points of the solve and matvec workload")
+    ap.add_argument("--sample-of", type=int, default=0,
+                    help="take the --n points at the density of this many points in the unit cube (a sub-cube "
+                         "with the same local geometry; used for small profiling cases); 0 = the unit cube")
     ap.add_argument("--length", type=float, default=0.05)
     ap.add_argument("--nugget", type=float, default=1e-3)
     ap.add_argument("--basis", default="skeleton", choices=["skeleton", "chebyshev"],
@@ -62,6 +65,9 @@ def parse():
     ap.add_argument("--cycle", default="V", choices=["V", "W", "F"])
     ap.add_argument("--nf", type=int, default=1)
     ap.add_argument("--nc", type=int, default=40)
+    ap.add_argument("--no-dd-residual", action="store_true",
+                    help="form the outer residual with the plain float64 product (its rounding floor at this "
+                         "size is about 1.7e-10, above the 1e-10 target)")
     ap.add_argument("--skip-square", action="store_true",
                     help="no smoothing on levels whose restriction is square (the leaf level here)")
     ap.add_argument("--no-autotune", action="store_true")
@@ -170,12 +176,14 @@ def whole_job_value(steps: int, world: int, ms: float) -> float:
 
 def workload_name(a):
     basis = f"skel64_tol{a.basis_tol:g}" if a.basis == "skeleton" else "q4"
-    return f"gauss3d_n{a.n}_l{a.length:g}_nug{a.nugget:g}_leaf64_{basis}_eta1"
+    dens = f"_density_of_{a.sample_of}" if a.sample_of else ""
+    return f"gauss3d_n{a.n}{dens}_l{a.length:g}_nug{a.nugget:g}_leaf64_{basis}_eta1"
 
 
 def solve_kw(a):
     return dict(tol=a.tol, max_cycles=a.max_cycles, n_f=a.nf, n_c=a.nc, precision=a.precision, outer=a.outer,
-                cycle=a.cycle, skip_square_levels=a.skip_square, use_graph=not a.no_graph)
+                cycle=a.cycle, skip_square_levels=a.skip_square, use_graph=not a.no_graph,
+                residual_dd=not a.no_dd_residual)
 
 
 def sample_points(a, n):
@@ -183,7 +191,7 @@ def sample_points(a, n):
     uniform sample in a cube of side (n / N)^(1/3) (the same local geometry, leaf
     sizes and far-field structure as the full workload)."""
     import workloads as W
-    return W.uniform_points(n, 3, 2) * (n / a.n) ** (1.0 / 3.0)
+    return W.uniform_points(n, 3, 2) * (n / (a.sample_of or a.n)) ** (1.0 / 3.0)
 
 
 def oracle_sample_time(a, n):
@@ -448,6 +456,8 @@ def main():
 
     # ---- the workload's matrix
     p = W.workload(2, n=a.n)
+    if a.sample_of:
+        p["points"] = p["points"] * (a.n / a.sample_of) ** (1.0 / 3.0)
     X = torch.from_numpy(p["points"]).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -525,6 +535,8 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    if os.environ.get("H2MG_BENCH_REPORT_LAUNCHES"):
+        print(f"launches before the timed steps: {pkg.H2Matrix.launch_count()}", file=sys.stderr, flush=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = pkg.H2Matrix.launch_count()
     with Clocks(local) as clk:
@@ -616,6 +628,7 @@ def main():
                        "nugget": a.nugget, "leaf": 64, "basis": a.basis, "basis_tol": a.basis_tol, "rank_max": 64,
                        "eta": 1.0, "tol": a.tol, "outer": a.outer, "cycle": a.cycle, "n_f": a.nf, "n_c": a.nc,
                        "skip_square_levels": a.skip_square, "coarse_level": a.coarse_level,
+                       "outer_residual": "float64 blocks, double-double sums" if not a.no_dd_residual else "float64",
                        "precision": a.precision, "storage": "f64 (+f32 copy)",
                        "l2": "inputs larger than L2 (stored blocks)", "build_s": build_s,
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -106,7 +106,11 @@ typedef struct {
     int rank_max;       /* SKELETON: rank cap, 1..64 */
 } h2mg_build_opts;
 
-typedef enum { H2MG_PREC_F64 = 0, H2MG_PREC_MIXED_F32 = 1 } h2mg_precision;
+/* Arithmetic of the V-cycle products (h2mg_solve_opts.precision) and of
+ * h2mg_apply_level. F64_DD (h2mg_apply_level at level 1 on float64 storage only): the
+ * float64 blocks with double-double vectors and sums, the product the extended-precision
+ * outer residual uses (h2mg_solve_opts.residual_dd). */
+typedef enum { H2MG_PREC_F64 = 0, H2MG_PREC_MIXED_F32 = 1, H2MG_PREC_F64_DD = 2 } h2mg_precision;
 typedef enum { H2MG_OUTER_VCYCLE = 0, H2MG_OUTER_FCG = 1, H2MG_OUTER_CG = 2 } h2mg_outer;
 /* Multigrid cycle of the outer loops. V: Algorithm 1 (Sec. 3.3). W and F, which the
  * paper names as further options after Algorithm 1: the textbook recursions, where
@@ -145,6 +149,12 @@ typedef struct {
                                        not a coarser operator: the V-cycle passes the
                                        residual through it. 0: Algorithm 1 literally */
     int cycle;                      /* h2mg_cycle */
+    int residual_dd;                /* 1: the outer residual b - A x is formed with double-double
+                                       vectors and sums over the float64 blocks (float64 storage
+                                       only; about five times the FP64 work of that product).
+                                       When |x| >> |b| (ill-conditioned systems) the float64 sum
+                                       rounds at about eps |A| |x|, which can exceed tol |b|;
+                                       this removes that floor. 0: float64 product */
 } h2mg_solve_opts;
 
 typedef struct {

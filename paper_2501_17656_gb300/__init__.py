@@ -24,7 +24,7 @@ library_path = os.path.join(_HERE, "libh2mg.so")
 KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "laplace_sl": 3, "poly": 4,
            "dmatern32_dl": 5}
 STORAGE = {"f64": 0, "df64": 1}
-PRECISION = {"f64": 0, "mixed_f32": 1}
+PRECISION = {"f64": 0, "mixed_f32": 1, "f64_dd": 2}
 OUTER = {"vcycle": 0, "fcg": 1, "cg": 2}
 CYCLE = {"V": 0, "W": 1, "F": 2}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5: "NOT_CONVERGED",
@@ -64,7 +64,8 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("n_f", ctypes.c_int),
                 ("n_c", ctypes.c_int), ("precision", ctypes.c_int),
                 ("explicit_restrict_residual", ctypes.c_int), ("outer", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("skip_square_levels", ctypes.c_int), ("cycle", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("skip_square_levels", ctypes.c_int), ("cycle", ctypes.c_int),
+                ("residual_dd", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -397,10 +398,10 @@ class H2Matrix:
 
     @staticmethod
     def _opts(tol=1e-10, max_cycles=100, n_f=1, n_c=40, precision="f64", explicit_restrict_residual=False,
-              outer="vcycle", use_graph=False, skip_square_levels=False, cycle="V"):
+              outer="vcycle", use_graph=False, skip_square_levels=False, cycle="V", residual_dd=False):
         return _SolveOpts(float(tol), int(max_cycles), int(n_f), int(n_c), PRECISION[precision],
                           int(bool(explicit_restrict_residual)), OUTER[outer], int(bool(use_graph)),
-                          int(bool(skip_square_levels)), CYCLE[cycle])
+                          int(bool(skip_square_levels)), CYCLE[cycle], int(bool(residual_dd)))
 
     def vcycle(self, x0, r1, **kw):
         _expect(x0, self.n, "x0", dev=self.device)

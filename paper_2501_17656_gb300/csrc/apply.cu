@@ -33,6 +33,8 @@ struct Ar<FMT_F64> {
   static constexpr int V = 2;
   using yo_t = double;       // type of the atomically accumulated row outputs
   __device__ static yo_t to_yo(double a) { return a; }
+  __device__ static void atomic_add(yo_t* p, double a) { atomicAdd(p, a); }
+  __device__ static double from_yo(yo_t v) { return v; }
   using vec_t = double;
   using mel_t = double;
   using acc_t = double;
@@ -56,6 +58,8 @@ struct Ar<FMT_DF> {
   static constexpr int V = 2;
   using yo_t = double;
   __device__ static yo_t to_yo(float2 a) { return (double)a.x + (double)a.y; }
+  __device__ static void atomic_add(yo_t* p, float2 a) { atomicAdd(p, to_yo(a)); }
+  __device__ static float2 from_yo(yo_t v) { return from_d(v); }
   using vec_t = float2;
   using mel_t = float2;
   using acc_t = float2;
@@ -87,6 +91,8 @@ struct Ar<FMT_F32> {
   static constexpr int V = 4;
   using yo_t = float;
   __device__ static yo_t to_yo(float a) { return a; }
+  __device__ static void atomic_add(yo_t* p, float a) { atomicAdd(p, a); }
+  __device__ static float from_yo(yo_t v) { return v; }
   using vec_t = float;
   using mel_t = float;
   using acc_t = float;
@@ -105,6 +111,37 @@ struct Ar<FMT_F32> {
   __device__ static vec_t out(acc_t a) { return a; }
   __device__ static double to_d(vec_t v) { return (double)v; }
   __device__ static vec_t from_d(double v) { return __double2float_rn(v); }
+};
+
+// Float64 blocks, double-double vectors and sums (the extended-precision residual).
+template <>
+struct Ar<FMT_DD> {
+  static constexpr int V = 2;
+  using yo_t = double2;
+  __device__ static yo_t to_yo(double2 a) { return a; }
+  __device__ static void atomic_add(yo_t* p, double2 a) { dd_atomic_add(p, a); }
+  __device__ static double2 from_yo(yo_t v) { return v; }
+  using vec_t = double2;
+  using mel_t = double;
+  using acc_t = double2;
+  using ld_t = double2;
+  __device__ static acc_t zero() { return make_double2(0.0, 0.0); }
+  __device__ static void decode(const ld_t& v, mel_t* m) {
+    m[0] = v.x;
+    m[1] = v.y;
+  }
+  __device__ static void fma(acc_t& a, mel_t m, vec_t x) { dd_fma(a.x, a.y, m, x.x, x.y); }
+  __device__ static void add(acc_t& a, acc_t b) { dd_add(a.x, a.y, b.x, b.y); }
+  __device__ static void norm(acc_t& a) { dd_norm(a.x, a.y); }
+  __device__ static acc_t shfl(acc_t a, int m) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
+  }
+  __device__ static vec_t out(acc_t a) {
+    dd_norm(a.x, a.y);
+    return a;
+  }
+  __device__ static double to_d(vec_t v) { return v.x + v.y; }
+  __device__ static vec_t from_d(double v) { return make_double2(v, 0.0); }
 };
 
 // NR consecutive elements from shared memory, as one vector load where the row is 8
@@ -236,12 +273,12 @@ __global__ void __launch_bounds__(256, bsgemv_min_ctas<FMT, NR>()) k_bsgemv(cons
               }
             }
             const int tt = lane & (CH - 1);
-            atomicAdd(yrow + ((int64_t)s * K + cl + CPP * (ch * CH + tt)) * NR + j, A::to_yo(A::out(zc[0][j])));
+            A::atomic_add(yrow + ((int64_t)s * K + cl + CPP * (ch * CH + tt)) * NR + j, A::out(zc[0][j]));
           } else {
 #pragma unroll
             for (int h = LPC / 2; h >= 1; h >>= 1) A::add(zc[0][j], A::shfl(zc[0][j], h));
             if ((lane % LPC) == 0)
-              atomicAdd(yrow + ((int64_t)s * K + cl + CPP * (ch * CH)) * NR + j, A::to_yo(A::out(zc[0][j])));
+              A::atomic_add(yrow + ((int64_t)s * K + cl + CPP * (ch * CH)) * NR + j, A::out(zc[0][j]));
           }
         }
       }
@@ -268,7 +305,7 @@ __global__ void __launch_bounds__(256, bsgemv_min_ctas<FMT, NR>()) k_bsgemv(cons
     acc_t s = red[0][i];
 #pragma unroll
     for (int ww = 1; ww < 8; ++ww) A::add(s, red[ww][i]);
-    atomicAdd(yrow + (int64_t)row * K * NR + i, A::to_yo(A::out(s)));
+    A::atomic_add(yrow + (int64_t)row * K * NR + i, A::out(s));
   }
 }
 
@@ -299,22 +336,43 @@ template <int FMT, class BT, int NR>
 __global__ void k_up_leaf(const BT* __restrict__ UT, int KD, int KC,
                           const typename Ar<FMT>::vec_t* __restrict__ xp,
                           typename Ar<FMT>::vec_t* __restrict__ xc) {
-  __shared__ double xs[64 * NR];
   int l = blockIdx.x;
-  for (int i = threadIdx.x; i < KD * NR; i += blockDim.x) xs[i] = Ar<FMT>::to_d(xp[(int64_t)l * KD * NR + i]);
-  __syncthreads();
   const BT* Ul = UT + (int64_t)l * KD * KC;
-  for (int b = threadIdx.x; b < KC; b += blockDim.x) {
-    double acc[NR];
+  if constexpr (FMT == FMT_DD) {   // double-double coefficients
+    __shared__ double2 xd[64 * NR];
+    for (int i = threadIdx.x; i < KD * NR; i += blockDim.x) xd[i] = xp[(int64_t)l * KD * NR + i];
+    __syncthreads();
+    for (int b = threadIdx.x; b < KC; b += blockDim.x) {
+      double2 acc[NR];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) acc[j] = 0.0;
-    for (int i = 0; i < KD; ++i) {
-      double u = (double)Ul[b + i * KC];
+      for (int j = 0; j < NR; ++j) acc[j] = make_double2(0.0, 0.0);
+      for (int i = 0; i < KD; ++i) {
+        const double u = (double)Ul[b + i * KC];
 #pragma unroll
-      for (int j = 0; j < NR; ++j) acc[j] += u * xs[i * NR + j];
+        for (int j = 0; j < NR; ++j) dd_fma(acc[j].x, acc[j].y, u, xd[i * NR + j].x, xd[i * NR + j].y);
+      }
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        dd_norm(acc[j].x, acc[j].y);
+        xc[((int64_t)l * KC + b) * NR + j] = acc[j];
+      }
     }
+  } else {
+    __shared__ double xs[64 * NR];
+    for (int i = threadIdx.x; i < KD * NR; i += blockDim.x) xs[i] = Ar<FMT>::to_d(xp[(int64_t)l * KD * NR + i]);
+    __syncthreads();
+    for (int b = threadIdx.x; b < KC; b += blockDim.x) {
+      double acc[NR];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) xc[((int64_t)l * KC + b) * NR + j] = Ar<FMT>::from_d(acc[j]);
+      for (int j = 0; j < NR; ++j) acc[j] = 0.0;
+      for (int i = 0; i < KD; ++i) {
+        double u = (double)Ul[b + i * KC];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[j] += u * xs[i * NR + j];
+      }
+#pragma unroll
+      for (int j = 0; j < NR; ++j) xc[((int64_t)l * KC + b) * NR + j] = Ar<FMT>::from_d(acc[j]);
+    }
   }
 }
 
@@ -540,7 +598,7 @@ __global__ void __launch_bounds__(256) k_down_multi(PassLevels pl, int steps,
       const int bb = idx / (K * NR), i = idx % (K * NR);
       const int cc = blockIdx.x * per + bb;
       if (cc >= pl.n[k]) continue;
-      acc_t acc = A::from_d((double)yrow[(int64_t)(pl.slot[k] + cc) * K * NR + i]);
+      acc_t acc = A::from_yo(yrow[(int64_t)(pl.slot[k] + cc) * K * NR + i]);
       if (pl.E[k])
         for (int q = 0; q < wpe; ++q) A::add(acc, sv[bb * wpb + q][i]);
       const vec_t o = A::out(acc);
@@ -584,27 +642,50 @@ __global__ void k_leaf_final(int KD, int KC, const typename Ar<FMT>::yo_t* __res
                              const int* __restrict__ leafoff, const int* __restrict__ perm,
                              double* __restrict__ y, int64_t ldy) {
   using A = Ar<FMT>;
-  __shared__ double ps[64 * NR];
   int l = blockIdx.x;
-  if (U)
-    for (int i = threadIdx.x; i < KC * NR; i += blockDim.x) ps[i] = A::to_d(yleaf[(int64_t)l * KC * NR + i]);
-  __syncthreads();
   int p0 = leafoff[l], nl = leafoff[l + 1] - p0;
-  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
-    double v[NR];
+  if constexpr (FMT == FMT_DD) {   // double-double sums, rounded to float64 on output
+    __shared__ double2 pd[64 * NR];
+    if (U)
+      for (int i = threadIdx.x; i < KC * NR; i += blockDim.x) pd[i] = yleaf[(int64_t)l * KC * NR + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+      double2 v[NR];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) v[j] = (double)yrow[((int64_t)l * KD + i) * NR + j];
-    if (U) {
-      const BT* Ul = U + (int64_t)l * KD * KC;
-      for (int b = 0; b < KC; ++b) {
-        double u = (double)Ul[i + b * KD];
+      for (int j = 0; j < NR; ++j) v[j] = yrow[((int64_t)l * KD + i) * NR + j];
+      if (U) {
+        const BT* Ul = U + (int64_t)l * KD * KC;
+        for (int b = 0; b < KC; ++b) {
+          const double u = (double)Ul[i + b * KD];
 #pragma unroll
-        for (int j = 0; j < NR; ++j) v[j] += u * ps[b * NR + j];
+          for (int j = 0; j < NR; ++j) dd_fma(v[j].x, v[j].y, u, pd[b * NR + j].x, pd[b * NR + j].y);
+        }
       }
-    }
-    const int64_t o = perm[p0 + i];
+      const int64_t o = perm[p0 + i];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) y[o + j * ldy] = v[j];
+      for (int j = 0; j < NR; ++j) y[o + j * ldy] = v[j].x + v[j].y;
+    }
+  } else {
+    __shared__ double ps[64 * NR];
+    if (U)
+      for (int i = threadIdx.x; i < KC * NR; i += blockDim.x) ps[i] = A::to_d(yleaf[(int64_t)l * KC * NR + i]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+      double v[NR];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) v[j] = (double)yrow[((int64_t)l * KD + i) * NR + j];
+      if (U) {
+        const BT* Ul = U + (int64_t)l * KD * KC;
+        for (int b = 0; b < KC; ++b) {
+          double u = (double)Ul[i + b * KD];
+#pragma unroll
+          for (int j = 0; j < NR; ++j) v[j] += u * ps[b * NR + j];
+        }
+      }
+      const int64_t o = perm[p0 + i];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) y[o + j * ldy] = v[j];
+    }
   }
 }
 
@@ -793,7 +874,7 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
   H2_CUDA(cudaMemsetAsync(yrow, 0, sizeof(yt) * (size_t)op.nrows * op.K * NR, s));
   // CTAs per block row: the autotuner's choice, else enough CTAs to fill the GPU when
   // the operator has few block rows
-  const int tuned = op.split[FMT][nr_index(NR)];
+  const int tuned = op.split[FMT == FMT_DD ? FMT_F64 : FMT][nr_index(NR)];
   const int split = force_split > 0 ? force_split : (tuned > 0 ? tuned : split_heuristic(op.nrows));
   const int grid = op.nrows * split;
   const void* const* blk = f32 ? op.blk32 : op.blk;
@@ -983,6 +1064,14 @@ void apply_level_multi(Matrix& M, int i, bool f32, const double* x, int64_t ldx,
 void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s) {
   int64_t n = level_size(M, i);
   apply_level_multi(M, i, f32, x, n, y, n, 1, s);
+}
+
+// y = A x at level 1 from the float64 blocks with double-double vectors and sums (one
+// column): the outer residual b - A x of a solve whose x is much larger than b, where
+// the float64 sum would round at the level of the residual itself.
+void apply_level1_dd(Matrix& M, const double* x, double* y, cudaStream_t s) {
+  H2_REQUIRE(M.fmt == FMT_F64, H2MG_ERR_INVALID_ARG, "the double-double product needs float64 storage");
+  apply_impl<FMT_DD, double, 1>(M, 1, x, M.n, y, M.n, s, M.d_U, M.d_UT);
 }
 
 // Level-1 product in the primary format with caller-supplied workspace (the

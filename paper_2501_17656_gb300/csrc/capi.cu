@@ -541,12 +541,16 @@ h2mg_status h2mg_apply_level(h2mg_matrix A, int level, int precision, const doub
     H2_REQUIRE(A && x && y, H2MG_ERR_INVALID_ARG, "null pointer argument");
     Matrix& M = A->M;
     H2_REQUIRE(level >= 1 && level <= M.lev, H2MG_ERR_INVALID_ARG, "level out of range");
-    H2_REQUIRE(precision == H2MG_PREC_F64 || (precision == H2MG_PREC_MIXED_F32 && M.with_f32),
-               H2MG_ERR_INVALID_ARG, "no FP32 copy");
+    H2_REQUIRE(precision == H2MG_PREC_F64 || (precision == H2MG_PREC_MIXED_F32 && M.with_f32) ||
+                   (precision == H2MG_PREC_F64_DD && level == 1 && M.fmt == FMT_F64),
+               H2MG_ERR_INVALID_ARG, "no FP32 copy, or double-double sums asked off level 1 / float64 storage");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t n = level_size(M, level);
     DevView X(x, n, true, s), Y(y, n, false, s);
-    apply_level(M, level, precision == H2MG_PREC_MIXED_F32, X.d, Y.d, s);
+    if (precision == H2MG_PREC_F64_DD)
+      apply_level1_dd(M, X.d, Y.d, s);
+    else
+      apply_level(M, level, precision == H2MG_PREC_MIXED_F32, X.d, Y.d, s);
     Y.copy_out(y, n, s);
     return H2MG_OK;
   });

@@ -161,9 +161,48 @@ __host__ __device__ inline int64_t swz(int i, int j, int K, int V) {
   return ((int64_t)(t * P + k) * 32 + lane) * V + sub;
 }
 
-// Element formats of stored blocks.
-enum Fmt { FMT_F64 = 0, FMT_DF = 1, FMT_F32 = 2 };
+// Element formats of stored blocks. FMT_DD is not a storage format: float64 blocks
+// read by a product whose vectors and sums are double-double (the extended-precision
+// outer residual).
+enum Fmt { FMT_F64 = 0, FMT_DF = 1, FMT_F32 = 2, FMT_DD = 3 };
 inline int fmt_bytes(int fmt) { return fmt == FMT_F32 ? 4 : 8; }
 inline int fmt_vec(int fmt) { return fmt == FMT_F32 ? 4 : 2; }
+
+// ----------------------------------------------------------------------------- double-double
+// A value hi + lo of two doubles: Dekker's product (exact through FMA) and Knuth's
+// two-sum give a ~106-bit accumulation; accumulators are kept unnormalised and
+// normalised when read out, like the double-float ones above.
+__device__ __forceinline__ void dd_fma(double& ah, double& al, double m, double xh, double xl) {
+  const double p = m * xh;
+  double e = fma(m, xh, -p);
+  e = fma(m, xl, e);
+  const double s = ah + p;
+  const double bb = s - ah;
+  const double err = (ah - (s - bb)) + (p - bb);
+  ah = s;
+  al = al + (err + e);
+}
+__device__ __forceinline__ void dd_add(double& ah, double& al, double bh, double bl) {
+  const double s = ah + bh;
+  const double bb = s - ah;
+  const double err = (ah - (s - bb)) + (bh - bb);
+  ah = s;
+  al = al + (err + bl);
+}
+__device__ __forceinline__ void dd_norm(double& ah, double& al) {
+  const double s = ah + al;
+  al = al - (s - ah);
+  ah = s;
+}
+// *p += v in double-double with two atomics: the hardware rounds old + v.x exactly as
+// two-sum's sum does, so the rounding error of this add is recovered from the returned
+// old value and added to the low word with v.y.
+__device__ __forceinline__ void dd_atomic_add(double2* p, double2 v) {
+  const double old = atomicAdd(&p->x, v.x);
+  const double s = old + v.x;
+  const double bb = s - old;
+  const double err = (old - (s - bb)) + (v.x - bb);
+  atomicAdd(&p->y, err + v.y);
+}
 
 }  // namespace h2mg

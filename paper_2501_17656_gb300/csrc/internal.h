@@ -179,6 +179,7 @@ struct ApplyWork {                // workspace of one product (see apply_impl)
 void setup_operators(Matrix& M);
 void apply_level1_ws(Matrix& M, const double* x, double* y, cudaStream_t s, const ApplyWork& ws);
 void apply_level1_ws_sizes(const Matrix& M, size_t* coef, size_t* pts);
+void apply_level1_dd(Matrix& M, const double* x, double* y, cudaStream_t s);
 void apply_level(Matrix& M, int i, bool f32, const double* x, double* y, cudaStream_t s);
 // Right-hand sides that one product, smoother, V-cycle or solve handles together.
 constexpr int NRMAX = 4;

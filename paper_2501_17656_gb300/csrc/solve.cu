@@ -653,6 +653,19 @@ static void axpy_cols(Matrix& M, const double* alpha, const double* x, double* y
   H2_LAUNCH_CHECK();
 }
 
+// The float64 outer residual r = b - A x for nr columns: the float64 product, or, with
+// o.residual_dd, the product with double-double sums (one launch sequence per column).
+static void outer_residual(Matrix& M, const h2mg_solve_opts& o, const double* b, const double* x, double* r,
+                           double* tmp, int64_t n, int nr, cudaStream_t s) {
+  if (o.residual_dd && M.fmt == FMT_F64) {
+    for (int c = 0; c < nr; ++c) apply_level1_dd(M, x + c * n, tmp + c * n, s);
+  } else {
+    apply_level_multi(M, 1, false, x, n, tmp, n, nr, s);
+  }
+  { k_sub<<<vec_grid(n * nr), 256, 0, s>>>(b, tmp, r, n * nr); ::h2mg::count_launch(); }
+  H2_LAUNCH_CHECK();
+}
+
 // y_c = x_c + beta[c] y_c with the coefficients from the host.
 static void xpby_cols(Matrix& M, const double* beta, const double* x, double* y, int64_t n, int nr, cudaStream_t s) {
   Work W = work(M);
@@ -724,9 +737,7 @@ static h2mg_status solve_cg_multi(Matrix& M, const double* b, double* x, int nr,
     xpby_cols(M, be, r, p, n, nr, s);                         // p = r + beta p
   }
   // the explicit float64 residual of the result
-  apply_level_multi(M, 1, false, x, n, W.t2, n, nr, s);
-  { k_sub<<<vec_grid(n * nr), 256, 0, s>>>(b, W.t2, r, n * nr); ::h2mg::count_launch(); }
-  H2_LAUNCH_CHECK();
+  outer_residual(M, o, b, x, r, W.t2, n, nr, s);
   double rr[NRMAX];
   dots_host(M, r, r, n, nr, rr, s);
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -775,9 +786,7 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
   }
   bool nan = false;
   for (int cyc = 0; cyc <= o.max_cycles; ++cyc) {
-    apply_level_multi(M, 1, false, x, n, W.t2, n, nr, s);
-    { k_sub<<<vec_grid(n * nr), 256, 0, s>>>(b, W.t2, r, n * nr); ::h2mg::count_launch(); }
-    H2_LAUNCH_CHECK();
+    outer_residual(M, o, b, x, r, W.t2, n, nr, s);
     dots_host(M, r, r, n, nr, rel, s);
     graph_collect(M);
     bool all = true;
@@ -939,9 +948,7 @@ h2mg_status solve_batched(const std::vector<Matrix*>& Ms, const double* const* b
       act[p] = !done[p];
       if (!act[p]) continue;
       const int64_t n = Ms[p]->n;
-      apply_level_multi(*Ms[p], 1, false, x[p], n, t2[p], n, 1, s);
-      { k_sub<<<vec_grid(n), 256, 0, s>>>(b[p], t2[p], r[p], n); ::h2mg::count_launch(); }
-      H2_LAUNCH_CHECK();
+      outer_residual(*Ms[p], o, b[p], x[p], r[p], t2[p], n, 1, s);
       va[p] = r[p];
       vb[p] = r[p];
     }
