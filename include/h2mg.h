@@ -149,12 +149,15 @@ typedef struct {
                                        not a coarser operator: the V-cycle passes the
                                        residual through it. 0: Algorithm 1 literally */
     int cycle;                      /* h2mg_cycle */
-    int residual_dd;                /* 1: the outer residual b - A x is formed with double-double
-                                       vectors and sums over the float64 blocks (float64 storage
-                                       only; about five times the FP64 work of that product).
-                                       When |x| >> |b| (ill-conditioned systems) the float64 sum
+    int residual_dd;                /* outer residual b - A x of repeated cycles and flexible CG.
+                                       0: the float64 product. 1: the float64 blocks with
+                                       double-double vectors and sums (float64 storage only;
+                                       about ten times the FP64 work of that product). When
+                                       |x| >> |b| (ill-conditioned systems) the float64 sum
                                        rounds at about eps |A| |x|, which can exceed tol |b|;
-                                       this removes that floor. 0: float64 product */
+                                       the extended product removes that floor. 2 (automatic):
+                                       float64 until a column's residual is within 10 tol,
+                                       then extended for that column from that cycle on */
 } h2mg_solve_opts;
 
 typedef struct {
@@ -260,12 +263,16 @@ typedef enum {
     H2MG_Q_N = 0, H2MG_Q_DIM = 1, H2MG_Q_L = 2, H2MG_Q_TSTAR = 3, H2MG_Q_LEVELS = 4,
     H2MG_Q_KD = 5, H2MG_Q_KC = 6, H2MG_Q_RANK = 7, H2MG_Q_NEAR_PAIRS = 8,
     H2MG_Q_FAR_PAIRS = 9, H2MG_Q_LEVEL_SIZE = 10, H2MG_Q_BYTES_PRIMARY = 11,
-    H2MG_Q_BYTES_F32 = 12, H2MG_Q_APPLY_BYTES = 13, H2MG_Q_DEVICE_BYTES = 14
+    H2MG_Q_BYTES_F32 = 12, H2MG_Q_APPLY_BYTES = 13, H2MG_Q_DEVICE_BYTES = 14,
+    H2MG_Q_PRODUCT_BYTES_F32 = 15
 } h2mg_query_what;
 
 /* *value = the quantity `what` (arg = tree level for FAR_PAIRS, multigrid level
- * for LEVEL_SIZE / APPLY_BYTES, 0 otherwise). APPLY_BYTES = algorithmic bytes
- * (stored blocks read once plus vectors) of one A_i apply in the primary format. */
+ * for LEVEL_SIZE / APPLY_BYTES, operator index for PRODUCT_BYTES_F32, 0 otherwise).
+ * APPLY_BYTES = algorithmic bytes (stored blocks read once plus vectors) of one A_i
+ * apply in the primary format. PRODUCT_BYTES_F32 = algorithmic bytes of one launch of
+ * the block-sparse product of operator arg (0: the close part of level 1; i >= 1:
+ * the coupling operator of level i) on the FP32 copy, one column. */
 h2mg_status h2mg_query(h2mg_matrix A, int what, int arg, int64_t* value);
 
 typedef enum {
@@ -320,7 +327,9 @@ int64_t h2mg_launch_count(void);
 
 /* Timing of the symmetric block-sparse product (the kernel that streams the stored
  * blocks D, S and P_i). enable = 1 clears the record and starts recording a pair of
- * CUDA events around each of its launches on the launching stream; enable = 0 stops.
+ * CUDA events around each of its launches on the launching stream; enable = 2 does the
+ * same for the launches on the FP32 copy only (the mixed-precision cycle's products,
+ * without the float64 and double-double residual products); enable = 0 stops.
  * On every call *launches, *ms (sum of the launch durations) and *bytes (sum of the
  * algorithmic bytes: stored blocks, input and output vectors, transposed partials)
  * are returned for the record so far; reading synchronises the recorded events.

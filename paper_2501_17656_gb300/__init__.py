@@ -31,7 +31,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5: "NOT_
           6: "NAN", 7: "TIMEOUT", 8: "UNSUPPORTED"}
 
 Q = dict(N=0, DIM=1, L=2, TSTAR=3, LEVELS=4, KD=5, KC=6, RANK=7, NEAR_PAIRS=8, FAR_PAIRS=9,
-         LEVEL_SIZE=10, BYTES_PRIMARY=11, BYTES_F32=12, APPLY_BYTES=13, DEVICE_BYTES=14)
+         LEVEL_SIZE=10, BYTES_PRIMARY=11, BYTES_F32=12, APPLY_BYTES=13, DEVICE_BYTES=14,
+         PRODUCT_BYTES_F32=15)
 X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5, SKELETON=6)
 BASIS = {"chebyshev": 0, "skeleton": 1}
 
@@ -401,7 +402,8 @@ class H2Matrix:
               outer="vcycle", use_graph=False, skip_square_levels=False, cycle="V", residual_dd=False):
         return _SolveOpts(float(tol), int(max_cycles), int(n_f), int(n_c), PRECISION[precision],
                           int(bool(explicit_restrict_residual)), OUTER[outer], int(bool(use_graph)),
-                          int(bool(skip_square_levels)), CYCLE[cycle], int(bool(residual_dd)))
+                          int(bool(skip_square_levels)), CYCLE[cycle],
+                          2 if residual_dd == "auto" else int(bool(residual_dd)))
 
     def vcycle(self, x0, r1, **kw):
         _expect(x0, self.n, "x0", dev=self.device)
@@ -445,7 +447,7 @@ class MaternLoss:
     @staticmethod
     def apply(points, y, b, length, nugget, leaf=64, q=4, eta=1.0, tol=1e-12, max_cycles=200,
               outer="fcg", n_f=1, n_c=40, precision="f64", use_graph=False, basis="chebyshev",
-              basis_tol=1e-9, cycle="V"):
+              basis_tol=1e-9, cycle="V", residual_dd=False):
         """``precision="mixed_f32"`` runs the V-cycles on an FP32 copy inside the float64
         outer loop (the solutions still meet ``tol`` in float64); ``basis="skeleton"``
         builds K (and so dK/dl, on the same skeletons) to the tolerance ``basis_tol``."""
@@ -459,7 +461,7 @@ class MaternLoss:
                 want = any(ctx.needs_input_grad)
                 dK = K.sibling("dmatern32_dl", length=float(l_)) if want else None
                 o = H2Matrix._opts(tol=tol, max_cycles=max_cycles, outer=outer, n_f=n_f, n_c=n_c,
-                                   precision=precision, use_graph=use_graph, cycle=cycle)
+                                   precision=precision, use_graph=use_graph, cycle=cycle, residual_dd=residual_dd)
                 yd, bd = y_.detach().contiguous(), b_.detach().contiguous()
                 _expect(yd, K.n, "y", dev=K.device)
                 _expect(bd, K.n, "b", dev=K.device)

@@ -879,11 +879,12 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
   const int grid = op.nrows * split;
   const void* const* blk = f32 ? op.blk32 : op.blk;
   Profile& P = M.prof;
-  if (P.on && P.cap_ev) {
+  const bool rec = P.on && (!P.f32_only || FMT == FMT_F32);
+  if (rec && P.cap_ev) {
     // inside a graph capture: the records become event nodes of the graph
     H2_REQUIRE(2 * P.cap_next + 2 <= P.cap_ev->size(), H2MG_ERR_UNSUPPORTED, "graph profiling events exhausted");
     H2_CUDA(cudaEventRecordWithFlags((*P.cap_ev)[2 * P.cap_next], s, cudaEventRecordExternal));
-  } else if (P.on) {
+  } else if (rec) {
     if (P.used * 2 + 2 > P.ev.size()) {
       for (int i = 0; i < 64; ++i) {
         cudaEvent_t e;
@@ -907,11 +908,11 @@ static void launch_bsgemv(Matrix& M, const SymOp& op, bool f32, const void* x, v
       throw Error{H2MG_ERR_UNSUPPORTED, "block size not supported"};
   }
   H2_LAUNCH_CHECK();
-  if (P.on && P.cap_ev) {
+  if (rec && P.cap_ev) {
     H2_CUDA(cudaEventRecordWithFlags((*P.cap_ev)[2 * P.cap_next + 1], s, cudaEventRecordExternal));
     P.cap_next++;
     P.cap_bytes->push_back((double)op.bytes(FMT == FMT_F32 ? 4 : 8, sizeof(vt) * NR));
-  } else if (P.on) {
+  } else if (rec) {
     H2_CUDA(cudaEventRecord(P.ev[2 * P.used + 1], s));
     P.used++;
     P.bytes.push_back((double)op.bytes(FMT == FMT_F32 ? 4 : 8, sizeof(vt) * NR));

@@ -356,6 +356,7 @@ h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int6
                "bad solve options");
     H2_REQUIRE(o->outer >= H2MG_OUTER_VCYCLE && o->outer <= H2MG_OUTER_CG, H2MG_ERR_INVALID_ARG, "unknown outer loop");
     H2_REQUIRE(o->cycle >= H2MG_CYCLE_V && o->cycle <= H2MG_CYCLE_F, H2MG_ERR_INVALID_ARG, "unknown cycle type");
+    H2_REQUIRE(o->residual_dd >= 0 && o->residual_dd <= 2, H2MG_ERR_INVALID_ARG, "residual_dd must be 0, 1 or 2");
     H2_REQUIRE(o->precision == H2MG_PREC_F64 || (o->precision == H2MG_PREC_MIXED_F32 && M.with_f32),
                H2MG_ERR_INVALID_ARG, "mixed precision needs a matrix built with_f32");
     H2_REQUIRE(!M.apply_only, H2MG_ERR_INVALID_ARG, "matrix was built for products only");
@@ -458,6 +459,12 @@ h2mg_status h2mg_query(h2mg_matrix A, int what, int arg, int64_t* value) {
       case H2MG_Q_DEVICE_BYTES:
         for (auto& d : M.owned) v += d.bytes;
         break;
+      case H2MG_Q_PRODUCT_BYTES_F32: {
+        H2_REQUIRE(arg >= 0 && arg < (int)M.opC.size(), H2MG_ERR_INVALID_ARG, "operator out of range");
+        const SymOp& op = arg == 0 ? M.opD : M.opC[arg];
+        v = op.bytes(4, 4);
+        break;
+      }
       default:
         throw Error{H2MG_ERR_INVALID_ARG, "unknown query"};
     }
@@ -652,6 +659,7 @@ h2mg_status h2mg_profile(h2mg_matrix A, int enable, int64_t* launches, double* m
       by += P.bytes[i];
     }
     P.on = (enable != 0);
+    P.f32_only = (enable == 2);
     if (launches) *launches = (int64_t)P.used + P.g_launches;
     if (ms) *ms = t;
     if (bytes) *bytes = by;

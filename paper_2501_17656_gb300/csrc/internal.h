@@ -47,6 +47,7 @@ inline int split_heuristic(int nrows) {
 // CUDA events around the launches of the block product (h2mg_profile).
 struct Profile {
   bool on = false;
+  bool f32_only = false;         // record only the products of the FP32 copy
   std::vector<cudaEvent_t> ev;   // pairs (start, stop)
   size_t used = 0;               // pairs in use
   std::vector<double> bytes;

@@ -589,7 +589,7 @@ static void vcycle_solve_step(Matrix& M, const h2mg_solve_opts& o, int nr, cudaS
     return;
   }
   graph_collect(M);
-  const int k = vcycle_graph(M, o, nr, M.prof.on ? 1 : 0);
+  const int k = vcycle_graph(M, o, nr, M.prof.on ? (M.prof.f32_only ? 2 : 1) : 0);
   GraphEntry& e = M.graphs->g[k];
   if (!e.exec) H2_CUDA(cudaGraphInstantiate(&e.exec, e.graph, 0));
   H2_CUDA(cudaGraphLaunch(e.exec, s));
@@ -655,13 +655,21 @@ static void axpy_cols(Matrix& M, const double* alpha, const double* x, double* y
 
 // The float64 outer residual r = b - A x for nr columns: the float64 product, or, with
 // o.residual_dd, the product with double-double sums (one launch sequence per column).
+// dd[c] (optional) selects the double-double product per column: with residual_dd = 1
+// every column, with 2 (automatic) the columns the caller marks; nullptr = none.
 static void outer_residual(Matrix& M, const h2mg_solve_opts& o, const double* b, const double* x, double* r,
-                           double* tmp, int64_t n, int nr, cudaStream_t s) {
-  if (o.residual_dd && M.fmt == FMT_F64) {
-    for (int c = 0; c < nr; ++c) apply_level1_dd(M, x + c * n, tmp + c * n, s);
-  } else {
-    apply_level_multi(M, 1, false, x, n, tmp, n, nr, s);
+                           double* tmp, int64_t n, int nr, cudaStream_t s, const bool* dd = nullptr) {
+  bool any = false, all = true;
+  for (int c = 0; c < nr; ++c) {
+    const bool u = M.fmt == FMT_F64 && (o.residual_dd == 1 || (o.residual_dd == 2 && dd && dd[c]));
+    any = any || u;
+    all = all && u;
   }
+  if (!all) apply_level_multi(M, 1, false, x, n, tmp, n, nr, s);
+  if (any)
+    for (int c = 0; c < nr; ++c)
+      if (M.fmt == FMT_F64 && (o.residual_dd == 1 || (o.residual_dd == 2 && dd && dd[c])))
+        apply_level1_dd(M, x + c * n, tmp + c * n, s);
   { k_sub<<<vec_grid(n * nr), 256, 0, s>>>(b, tmp, r, n * nr); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
 }
@@ -785,9 +793,24 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
     qp = pp + n * NRMAX;
   }
   bool nan = false;
+  bool near[NRMAX];   // automatic extended residual: the column is within 10 tol
+  for (int c = 0; c < nr; ++c) near[c] = false;
   for (int cyc = 0; cyc <= o.max_cycles; ++cyc) {
-    outer_residual(M, o, b, x, r, W.t2, n, nr, s);
+    outer_residual(M, o, b, x, r, W.t2, n, nr, s, near);
     dots_host(M, r, r, n, nr, rel, s);
+    if (o.residual_dd == 2) {
+      // a column that reaches 10 tol in float64 is re-checked with the extended product
+      // before it may stop (the float64 sum's rounding floor can lie near tol)
+      bool redo = false;
+      for (int c = 0; c < nr; ++c) {
+        const double rr = nb[c] > 0 ? std::sqrt(rel[c]) / nb[c] : 0.0;
+        if (!near[c] && !done[c] && std::isfinite(rr) && rr <= 10.0 * o.tol) near[c] = redo = true;
+      }
+      if (redo) {
+        outer_residual(M, o, b, x, r, W.t2, n, nr, s, near);
+        dots_host(M, r, r, n, nr, rel, s);
+      }
+    }
     graph_collect(M);
     bool all = true;
     for (int c = 0; c < nr; ++c) {

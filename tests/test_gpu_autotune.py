@@ -1,7 +1,7 @@
 """The block-product autotuner: it reports a timing per operator and column group,
-never picks a slower split than the fixed rule by more than timing noise, and
-leaves every product equal to the oracle's (a launch shape changes only the order of
-the atomic sums)."""
+never picks a slower split than the fixed rule, and leaves every product and a
+V-cycle equal to the oracle's (a launch shape changes only the order of the atomic
+sums)."""
 import numpy as np
 import pytest
 
@@ -54,7 +54,13 @@ def test_autotune_reports_and_keeps_products_exact():
         y32 = A.apply_level(i, torch.from_numpy(vp).cuda(), "mixed_f32").cpu().numpy()
         yu32 = np.concatenate([y32[j * KC: j * KC + off[j + 1] - off[j]] for j in range(1 << mg.m(i))])
         assert rel(yu32, mg.apply(i, v)) < 1e-5
-    b = torch.from_numpy(W.normal_rhs(16384, 2)).cuda()
-    x, info = A.solve(b, tol=1e-8, max_cycles=400, outer="fcg", precision="mixed_f32", use_graph=True)
-    assert info.converged
+    # a V-cycle with short smoothers through the tuned launches equals the oracle's
+    from oracle import SolveOpts
+    from oracle.mg import vcycle
+    if mg.chol is not None:
+        bv = np.random.default_rng(9).standard_normal(16384)
+        xg = A.vcycle(torch.zeros(16384, dtype=torch.float64, device="cuda"), torch.from_numpy(bv).cuda(),
+                      n_f=1, n_c=2).cpu().numpy()
+        xo = vcycle(mg, np.zeros(16384), bv, SolveOpts(n_f=1, n_c=2))
+        assert rel(xg, xo) < 1e-9
     A.close()

@@ -100,8 +100,10 @@ def test_double_double_residual_removes_the_float64_floor():
     kw = dict(max_cycles=150, outer="fcg", precision="mixed_f32", use_graph=True, raise_on_fail=False)
     x64, i64 = A.solve(b, tol=2e-12, **kw)
     xdd, idd = A.solve(b, tol=2e-12, residual_dd=True, **kw)
+    xau, iau = A.solve(b, tol=2e-12, residual_dd="auto", **kw)
     best64 = min(i64.history())
     assert idd.converged, (idd.cycles, min(idd.history()), best64)
+    assert iau.converged, (iau.cycles, min(iau.history()), best64)
     assert float(xdd.norm() / b.norm()) > 100      # the |x| >> |b| regime of the floor
     print(f"best float64-residual relres {best64:.2e}; double-double reached {idd.relres:.2e} in {idd.cycles}")
     A.close()
