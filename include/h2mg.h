@@ -156,8 +156,9 @@ typedef struct {
                                        |x| >> |b| (ill-conditioned systems) the float64 sum
                                        rounds at about eps |A| |x|, which can exceed tol |b|;
                                        the extended product removes that floor. 2 (automatic):
-                                       float64 until a column's residual is within 10 tol,
-                                       then extended for that column from that cycle on */
+                                       float64 until a column's residual is within 100 tol or
+                                       has made no new minimum for 5 cycles, then extended for
+                                       that column from that cycle on */
 } h2mg_solve_opts;
 
 typedef struct {

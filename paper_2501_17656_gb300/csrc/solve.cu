@@ -793,18 +793,32 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
     qp = pp + n * NRMAX;
   }
   bool nan = false;
-  bool near[NRMAX];   // automatic extended residual: the column is within 10 tol
-  for (int c = 0; c < nr; ++c) near[c] = false;
+  bool near[NRMAX];   // automatic extended residual: switched on for this column
+  double best[NRMAX];
+  int since[NRMAX];
+  for (int c = 0; c < nr; ++c) {
+    near[c] = false;
+    best[c] = INFINITY;
+    since[c] = 0;
+  }
   for (int cyc = 0; cyc <= o.max_cycles; ++cyc) {
     outer_residual(M, o, b, x, r, W.t2, n, nr, s, near);
     dots_host(M, r, r, n, nr, rel, s);
     if (o.residual_dd == 2) {
-      // a column that reaches 10 tol in float64 is re-checked with the extended product
-      // before it may stop (the float64 sum's rounding floor can lie near tol)
+      // a column switches to the extended product once its float64 residual is within
+      // 100 tol, or has not reached a new minimum for 5 cycles (the float64 sum's
+      // rounding floor, which can lie near or above tol); this cycle is re-checked
       bool redo = false;
       for (int c = 0; c < nr; ++c) {
         const double rr = nb[c] > 0 ? std::sqrt(rel[c]) / nb[c] : 0.0;
-        if (!near[c] && !done[c] && std::isfinite(rr) && rr <= 10.0 * o.tol) near[c] = redo = true;
+        if (near[c] || done[c] || !std::isfinite(rr)) continue;
+        if (rr < best[c]) {
+          best[c] = rr;
+          since[c] = 0;
+        } else {
+          ++since[c];
+        }
+        if (rr <= 100.0 * o.tol || since[c] >= 5) near[c] = redo = true;
       }
       if (redo) {
         outer_residual(M, o, b, x, r, W.t2, n, nr, s, near);
