@@ -74,6 +74,7 @@ def parse():
                     help="no smoothing on levels whose restriction is square (the leaf level here)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-matvec", action="store_true")
+    ap.add_argument("--no-panel", action="store_true", help="skip the 128-column tensor-core product")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=8192,
                     help="points of the oracle's sample (a sub-cube at the workload's density)")
@@ -460,6 +461,38 @@ def bem_vs_cg(a, pkg, W, torch):
     return out
 
 
+def panel_product(A, a, torch, stream, pk):
+    """128 right-hand sides on the full matrix: the tensor-core product (split TF32; each
+    stored block read twice per 128 columns) against the FP32 CUDA-core product (four
+    columns per block read), per column, with both errors against float64 on 4 columns."""
+    import numpy as np
+    n = a.n
+    X = torch.randn(128, n, dtype=torch.float64, device="cuda").t()
+    Y = torch.zeros(128, n, dtype=torch.float64, device="cuda").t()
+    t0 = time.perf_counter()
+    A.apply(X, y=Y, precision="tf32x3")          # first call builds the block lists and panels
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    ms_tc, _ = timed(stream, lambda: A.apply(X, y=Y, precision="tf32x3"), 3)
+    ytc = Y[:, :4].cpu().numpy()
+    ms_f32, _ = timed(stream, lambda: A.apply(X, y=Y, precision="mixed_f32"))
+    yf = Y[:, :4].cpu().numpy()
+    y64 = A.apply(X[:, :4]).cpu().numpy()
+    entries = A.query("PANEL_ENTRIES")
+    flops = entries * 3 * 2 * 128 * 64 * 64
+    tf32_peak = pk["bf16_tflops"] * 1.1 / 2.25
+    err = lambda y: float(np.max(np.linalg.norm(y - y64, axis=0) / np.linalg.norm(y64, axis=0)))
+    del X, Y
+    torch.cuda.empty_cache()
+    return {"nrhs": 128, "ms_tensor_core": ms_tc, "ms_cuda_core_f32": ms_f32,
+            "ms_per_column_tensor_core": ms_tc / 128, "ms_per_column_cuda_core_f32": ms_f32 / 128,
+            "per_column_speedup": ms_f32 / ms_tc, "block_panel_products": entries,
+            "tf32_tflops_issued": flops / ms_tc / 1e9, "tf32_peak_tflops": tf32_peak,
+            "tf32_peak_source": "measured bf16 burst x nominal TF32/BF16 ratio (1.1/2.25)",
+            "rel_err_vs_f64_tensor_core": err(ytc), "rel_err_vs_f64_cuda_core_f32": err(yf),
+            "setup_s": setup_s}
+
+
 def timed(stream, fn, reps=1):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -549,6 +582,12 @@ def main():
             yh = A.apply_level(1, xv, prec).cpu().numpy()
             matvec[prec]["oracle_rows_rel_err"] = float(np.linalg.norm(yh[rows] - yr) / np.linalg.norm(yr))
         del xv, yv
+        if a.precision == "mixed_f32" and not a.no_panel:
+            try:
+                matvec["panel_128rhs"] = panel_product(A, a, torch, stream, pk)
+            except Exception as e:  # noqa: BLE001  (a secondary measurement: recorded, not raised)
+                torch.cuda.synchronize()
+                matvec["panel_128rhs"] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     # ---- one complete solve: the cycle count of a solve, its convergence and its own time
     b = torch.from_numpy(p["b"]).cuda()
@@ -557,7 +596,8 @@ def main():
     msf, (x, finfo) = timed(stream, lambda: A.solve(b, raise_on_fail=False, **kw))
     cycles = finfo.cycles
     full = {"s": msf / 1e3, "solves_per_s": 1e3 / msf, "cycles": cycles, "converged": bool(finfo.converged),
-            "relres": finfo.relres, "s_per_cycle": msf / 1e3 / max(cycles, 1)}
+            "relres": finfo.relres, "s_per_cycle": msf / 1e3 / max(cycles, 1),
+            "history": [float(f"{h:.3g}") for h in finfo.history()]}
     relres_check = float(((b - A.apply(x)).norm() / b.norm()).item())
     # the solution against the exact kernel matrix on sampled rows (the oracle's formula)
     xs = x.cpu().numpy()
@@ -688,7 +728,8 @@ def main():
                        "nugget": a.nugget, "leaf": 64, "basis": a.basis, "basis_tol": a.basis_tol, "rank_max": 64,
                        "eta": 1.0, "tol": a.tol, "outer": a.outer, "cycle": a.cycle, "n_f": a.nf, "n_c": a.nc,
                        "skip_square_levels": a.skip_square, "coarse_level": a.coarse_level,
-                       "outer_residual": "float64, then double-double sums once within 100 tol or stagnant"
+                       "outer_residual": "float64, then double-double sums once within 100 tol or once a "
+                                         "probe shows the float64 residual is mostly rounding"
                        if not a.no_dd_residual else "float64",
                        "precision": a.precision, "storage": "f64 (+f32 copy)",
                        "l2": "inputs larger than L2 (stored blocks)", "build_s": build_s,

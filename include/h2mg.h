@@ -110,7 +110,7 @@ typedef struct {
  * h2mg_apply_level. F64_DD (h2mg_apply_level at level 1 on float64 storage only): the
  * float64 blocks with double-double vectors and sums, the product the extended-precision
  * outer residual uses (h2mg_solve_opts.residual_dd). */
-typedef enum { H2MG_PREC_F64 = 0, H2MG_PREC_MIXED_F32 = 1, H2MG_PREC_F64_DD = 2 } h2mg_precision;
+typedef enum { H2MG_PREC_F64 = 0, H2MG_PREC_MIXED_F32 = 1, H2MG_PREC_F64_DD = 2, H2MG_PREC_TF32X3 = 3 } h2mg_precision;
 typedef enum { H2MG_OUTER_VCYCLE = 0, H2MG_OUTER_FCG = 1, H2MG_OUTER_CG = 2 } h2mg_outer;
 /* Multigrid cycle of the outer loops. V: Algorithm 1 (Sec. 3.3). W and F, which the
  * paper names as further options after Algorithm 1: the textbook recursions, where
@@ -156,9 +156,12 @@ typedef struct {
                                        |x| >> |b| (ill-conditioned systems) the float64 sum
                                        rounds at about eps |A| |x|, which can exceed tol |b|;
                                        the extended product removes that floor. 2 (automatic):
-                                       float64 until a column's residual is within 100 tol or
-                                       has made no new minimum for 5 cycles, then extended for
-                                       that column from that cycle on */
+                                       float64 until a column's residual is within 100 tol,
+                                       then extended for that column from that cycle on; a
+                                       column whose float64 residual makes no new minimum for
+                                       5 cycles is probed with one extended residual and
+                                       switches if that is below 0.8 of the float64 one (the
+                                       float64 value is mostly rounding) */
 } h2mg_solve_opts;
 
 typedef struct {
@@ -187,6 +190,25 @@ h2mg_status h2mg_build(const double* points, int64_t n, int dim, const h2mg_kern
 h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int64_t ld,
                        void* stream);
 
+/* Y = A X (Sec. 3.1) in a chosen arithmetic, nrhs >= 1 columns, leading dimension
+ * ld >= n, host or device buffers (not overlapping):
+ *   H2MG_PREC_F64        the primary storage, as h2mg_apply;
+ *   H2MG_PREC_MIXED_F32  the FP32 copy on the CUDA cores, four columns per block read;
+ *   H2MG_PREC_TF32X3     the FP32 copy on the tensor cores (tcgen05), 128 columns per
+ *                        block read: every step of the product -- U_l^T x_l and E_c^T x_c
+ *                        upward, the near and coupling blocks, E_c y_p and U_l y_l
+ *                        downward -- is a 64 x 64 block times a 64 x 128 panel. Each FP32
+ *                        operand a is split into a TF32 head h = tf32(a) and tail
+ *                        t = tf32(a - h), and a b is formed as h_a h_b + h_a t_b + t_a h_b
+ *                        in FP32 (relative error of each product below about 2^-21).
+ *                        Needs leaf and rank blocks of 64 (KD = KC = 64). Each
+ *                        off-diagonal stored block is read twice (once per triangle), so
+ *                        that no output needs atomic sums. Synchronises the stream.
+ * Errors: INVALID_ARG (unknown precision, no FP32 copy for MIXED_F32 / TF32X3),
+ * UNSUPPORTED (TF32X3 with blocks other than 64), CUDA. */
+h2mg_status h2mg_apply_ex(h2mg_matrix A, int precision, const double* x, double* y, int nrhs, int64_t ld,
+                          void* stream);
+
 /* Solve A x = b with H2-MG (Algorithm 1, repeated V-cycles, Sec. 3.3). On entry
  * x holds the initial guess x_0 (zeros are the paper's choice), on exit the
  * solution. nrhs >= 1 columns, leading dimension ld. Columns are solved in groups
@@ -213,11 +235,14 @@ h2mg_status h2mg_solve_batched(int nprob, const h2mg_matrix* A, const double* co
                                const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream);
 
 /* Build the H2 matrix of another kernel on the same points with the same cluster
- * tree, block partition, Chebyshev nodes and orthonormalisation factors as A
- * (Sec. 3.1 form with A's bases; only D and the couplings S = R k'(xi, xi) R^T
- * change). With H2MG_K_DMATERN32_DL (length = A's length, nugget 0) this is
- * d A / d length of a Matern-3/2 H2 matrix: since the interpolation bases do not
- * depend on the kernel's parameters, it is the exact derivative of A's H2 form.
+ * tree and block partition as A (Sec. 3.1). With Chebyshev bases it also shares A's
+ * nodes and orthonormalisation factors (only D and the couplings S = R k'(xi, xi) R^T
+ * change); with H2MG_K_DMATERN32_DL (length = A's length, nugget 0) it is then
+ * d A / d length of a Matern-3/2 H2 matrix exactly, since interpolation bases do not
+ * depend on the kernel's parameters. Skeleton bases are chosen from A's kernel values
+ * and do not span another kernel's far field: a sibling of a skeleton matrix
+ * skeletonizes its own kernel (same tolerance and rank cap) on A's tree and
+ * partition, and approximates d A / d length of the exact kernel to that tolerance.
  * The result supports products only (h2mg_apply, h2mg_apply_level at level 1);
  * h2mg_solve on it returns INVALID_ARG. It refers to A's device structures:
  * destroy it before A. Weights and diagonal overrides of k are not supported
@@ -265,7 +290,7 @@ typedef enum {
     H2MG_Q_KD = 5, H2MG_Q_KC = 6, H2MG_Q_RANK = 7, H2MG_Q_NEAR_PAIRS = 8,
     H2MG_Q_FAR_PAIRS = 9, H2MG_Q_LEVEL_SIZE = 10, H2MG_Q_BYTES_PRIMARY = 11,
     H2MG_Q_BYTES_F32 = 12, H2MG_Q_APPLY_BYTES = 13, H2MG_Q_DEVICE_BYTES = 14,
-    H2MG_Q_PRODUCT_BYTES_F32 = 15
+    H2MG_Q_PRODUCT_BYTES_F32 = 15, H2MG_Q_PANEL_ENTRIES = 16
 } h2mg_query_what;
 
 /* *value = the quantity `what` (arg = tree level for FAR_PAIRS, multigrid level
@@ -273,7 +298,9 @@ typedef enum {
  * APPLY_BYTES = algorithmic bytes (stored blocks read once plus vectors) of one A_i
  * apply in the primary format. PRODUCT_BYTES_F32 = algorithmic bytes of one launch of
  * the block-sparse product of operator arg (0: the close part of level 1; i >= 1:
- * the coupling operator of level i) on the FP32 copy, one column. */
+ * the coupling operator of level i) on the FP32 copy, one column. PANEL_ENTRIES =
+ * block-times-panel products of one 128-column pass of the tensor-core product
+ * (h2mg_apply_ex, TF32X3), 0 before its first call. */
 h2mg_status h2mg_query(h2mg_matrix A, int what, int arg, int64_t* value);
 
 typedef enum {

@@ -5,10 +5,14 @@ L(y, b, theta) = 1/2 y^T A^{-1} y + 1^T A^{-1} b with A the H2 matrix of the
 Matern-3/2 kernel (1 + sqrt3 r/l) exp(-sqrt3 r/l) plus nugget s. With a = A^{-1} y,
 x = A^{-1} b and w = A^{-1} 1 (A symmetric):
     dL/dy = a,  dL/db = w,  dL/dtheta = -1/2 a^T (dA/dtheta) a - w^T (dA/dtheta) x,
-with dA/ds = I and dA/dl the H2 matrix of the derivative kernel (3 r^2/l^3) exp(-sqrt3 r/l)
-built with the same tree, nodes and orthonormalisation factors as A: the interpolation
-bases do not depend on theta, so this is the exact derivative of A's H2 form. The
-solves here are dense (np.linalg.solve of the H2 matrix), small N only.
+with dA/ds = I and dA/dl the H2 matrix of the derivative kernel (3 r^2/l^3) exp(-sqrt3 r/l).
+With Chebyshev bases it is built with the same tree, nodes and orthonormalisation
+factors as A: interpolation bases do not depend on theta, so it is the exact derivative of
+A's H2 form. Skeleton bases are selected from A's own kernel values and would not
+represent the derivative kernel's far field; there dA/dl is the derivative kernel's own
+skeleton H2 matrix on A's tree (same tolerance and rank cap), an approximation of the
+exact kernel's derivative to that tolerance. The solves here are dense (np.linalg.solve
+of the H2 matrix), small N only.
 """
 from __future__ import annotations
 
@@ -20,7 +24,11 @@ from .h2 import H2Matrix, KernelSpec
 
 
 def derivative_h2(h: H2Matrix, kspec: KernelSpec) -> H2Matrix:
-    """The H2 matrix of kernel ``kspec`` with h's tree, partition, nodes and bases."""
+    """The H2 matrix of kernel ``kspec`` with h's tree and partition: with h's nodes and
+    bases (Chebyshev), or with skeletons of its own (skeleton bases)."""
+    if h.basis == "skeleton":
+        return H2Matrix(h.X, kspec, h.leaf, h.q, h.eta, tree=h.tree, partition=(h.far, h.inadm), basis="skeleton",
+                        tol=h.tol, rank_max=h.rank_max)
     d = copy.copy(h)
     d.kspec = kspec
     d._cache = {k: v for k, v in h._cache.items() if k[0] == "off"}

@@ -24,7 +24,7 @@ library_path = os.path.join(_HERE, "libh2mg.so")
 KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "laplace_sl": 3, "poly": 4,
            "dmatern32_dl": 5}
 STORAGE = {"f64": 0, "df64": 1}
-PRECISION = {"f64": 0, "mixed_f32": 1, "f64_dd": 2}
+PRECISION = {"f64": 0, "mixed_f32": 1, "f64_dd": 2, "tf32x3": 3}
 OUTER = {"vcycle": 0, "fcg": 1, "cg": 2}
 CYCLE = {"V": 0, "W": 1, "F": 2}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5: "NOT_CONVERGED",
@@ -32,7 +32,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5: "NOT_
 
 Q = dict(N=0, DIM=1, L=2, TSTAR=3, LEVELS=4, KD=5, KC=6, RANK=7, NEAR_PAIRS=8, FAR_PAIRS=9,
          LEVEL_SIZE=10, BYTES_PRIMARY=11, BYTES_F32=12, APPLY_BYTES=13, DEVICE_BYTES=14,
-         PRODUCT_BYTES_F32=15)
+         PRODUCT_BYTES_F32=15, PANEL_ENTRIES=16)
 X = dict(PERM=0, LEAF_OFFSETS=1, NEAR=2, FAR=3, RANKS=4, BOXES=5, SKELETON=6)
 BASIS = {"chebyshev": 0, "skeleton": 1}
 
@@ -40,7 +40,7 @@ EXPORTED = ["h2mg_build", "h2mg_apply", "h2mg_solve", "h2mg_destroy", "h2mg_erro
             "h2mg_last_error", "h2mg_query", "h2mg_export", "h2mg_apply_level",
             "h2mg_coarse_solve", "h2mg_smooth", "h2mg_vcycle", "h2mg_launch_count", "h2mg_profile",
             "h2mg_transfer", "h2mg_apply_noalloc", "h2mg_build_sibling", "h2mg_dot", "h2mg_solve_batched",
-            "h2mg_autotune", "h2mg_matern_loss_grad"]
+            "h2mg_autotune", "h2mg_matern_loss_grad", "h2mg_apply_ex"]
 
 
 class H2MGError(RuntimeError):
@@ -96,6 +96,7 @@ def load_library(build_if_missing: bool = False):
     lib.h2mg_build.argtypes = [vp, i64, ci, ctypes.POINTER(_Kernel), ctypes.POINTER(_BuildOpts), vp,
                                ctypes.POINTER(vp)]
     lib.h2mg_apply.argtypes = [vp, vp, vp, ci, i64, vp]
+    lib.h2mg_apply_ex.argtypes = [vp, ci, vp, vp, ci, i64, vp]
     lib.h2mg_solve.argtypes = [vp, vp, vp, ci, i64, ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.h2mg_destroy.argtypes = [vp]
     lib.h2mg_error_string.argtypes = [ci]
@@ -268,8 +269,9 @@ class H2Matrix:
 
     # ----------------------------------------------------------------- siblings
     def sibling(self, kernel: str, length: float = 1.0, nugget: float = 0.0, degree: int = 2) -> "H2Matrix":
-        """The H2 matrix of another kernel with this matrix's tree, partition, nodes and
-        bases (products only); e.g. ``sibling("dmatern32_dl", length)`` = dA/dlength."""
+        """The H2 matrix of another kernel on this matrix's tree and partition (products
+        only), with its nodes and bases when they are Chebyshev, with skeletons of its own
+        kernel when they are skeletons; e.g. ``sibling("dmatern32_dl", length)`` = dA/dlength."""
         k = _Kernel(KERNELS[kernel], float(length), float(nugget), int(degree), None, None)
         h = ctypes.c_void_p()
         _check(self._lib.h2mg_build_sibling(self._h, ctypes.byref(k), _stream(), ctypes.byref(h)))
@@ -334,9 +336,11 @@ class H2Matrix:
         return self.query("LEVEL_SIZE", i)
 
     # ----------------------------------------------------------------- products
-    def apply(self, x, y=None):
-        """y = A x for a vector or an (n, nrhs) block of columns; the columns go through
-        the products together, each stored block read once per group of four."""
+    def apply(self, x, y=None, precision: str | None = None):
+        """y = A x for a vector or an (n, nrhs) block of columns. Default: the primary
+        storage, the columns through the products in groups of four. ``precision``
+        "f64", "mixed_f32" (the FP32 copy on the CUDA cores) or "tf32x3" (the FP32 copy
+        on the tensor cores, 128 columns per block read; see h2mg_apply_ex)."""
         _expect(x, self.n, "x", cols=True, dev=self.device)
         xb, nrhs = _colmajor(x)
         out = y if y is not None else _new_cols(x, self.n, None if len(x.shape) == 1 else nrhs)
@@ -344,7 +348,11 @@ class H2Matrix:
         if tuple(out.shape) != tuple(x.shape):
             raise ValueError(f"y must have the shape of x {tuple(x.shape)}, got {tuple(out.shape)}")
         yb, _ = _colmajor(out)
-        _check(self._lib.h2mg_apply(self._h, _ptr(xb), _ptr(yb), nrhs, self.n, _stream()))
+        if precision is None:
+            _check(self._lib.h2mg_apply(self._h, _ptr(xb), _ptr(yb), nrhs, self.n, _stream()))
+        else:
+            _check(self._lib.h2mg_apply_ex(self._h, PRECISION[precision], _ptr(xb), _ptr(yb), nrhs, self.n,
+                                           _stream()))
         _copy_back(out, yb)
         return out
 

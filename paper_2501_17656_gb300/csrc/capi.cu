@@ -55,6 +55,7 @@ void best_effort(cudaError_t e, const char* what) {
 Matrix::~Matrix() {
   if (stream) best_effort(cudaStreamSynchronize(stream), "cudaStreamSynchronize (release)");
   destroy_graphs(*this);
+  destroy_panel_plan(*this);
   for (auto e : prof.ev) best_effort(cudaEventDestroy(e), "cudaEventDestroy (profile)");
   for (auto& d : owned)
     if (d.p) best_effort(cudaFree(d.p), "cudaFree (release)");
@@ -202,19 +203,29 @@ static void build_sibling(Matrix& B, const Matrix& A, const h2mg_kernel* k) {
   cudaStream_t s = B.stream;
   B.n = A.n; B.dim = A.dim; B.leaf = A.leaf; B.q = A.q; B.k = A.k; B.eta = A.eta;
   B.fmt = A.fmt; B.with_f32 = false; B.apply_only = true;
-  B.basis = A.basis; B.basis_tol = A.basis_tol; B.d_nsw = A.d_nsw; B.d_skel = A.d_skel;
+  B.basis = A.basis; B.basis_tol = A.basis_tol;
   B.L = A.L; B.KD = A.KD; B.KC = A.KC; B.tstar = A.tstar; B.lev_nat = A.lev_nat; B.lev = 1;
-  B.offsets = A.offsets; B.far = A.far; B.inadm = A.inadm; B.h_rank = A.h_rank;
+  B.offsets = A.offsets; B.far = A.far; B.inadm = A.inadm;
   B.d_perm = A.d_perm; B.d_slot_of = A.d_slot_of; B.d_leafoff = A.d_leafoff; B.d_X = A.d_X;
-  B.d_box = A.d_box; B.d_nodes = A.d_nodes; B.d_rank = A.d_rank;
-  B.d_U = A.d_U; B.d_E = A.d_E; B.d_R = A.d_R; B.d_UT = A.d_UT; B.d_ET = A.d_ET;
-  B.poolE = A.poolE;            // swizzled transfers (shared, not owned)
+  B.d_box = A.d_box;
+  // Chebyshev bases interpolate any smooth kernel and do not depend on the kernel's
+  // parameters: the sibling shares them, and dK/dtheta's H2 form is the exact derivative
+  // of K's. Skeleton bases are chosen from K's own values, which would not carry the
+  // derivative kernel's far field: the sibling skeletonizes its own kernel on the same
+  // tree and partition.
+  const bool own_bases = A.basis == H2MG_BASIS_SKELETON;
+  if (!own_bases) {
+    B.d_nsw = A.d_nsw; B.d_skel = A.d_skel; B.h_rank = A.h_rank; B.d_nodes = A.d_nodes; B.d_rank = A.d_rank;
+    B.d_U = A.d_U; B.d_E = A.d_E; B.d_R = A.d_R; B.d_UT = A.d_UT; B.d_ET = A.d_ET;
+    B.poolE = A.poolE;            // swizzled transfers (shared, not owned)
+  }
   B.d_flag = (int*)B.alloc(sizeof(int) * 4);
   B.d_sw = (double*)B.alloc(sizeof(double) * B.n);
   B.d_dg = (double*)B.alloc(sizeof(double) * B.n);
   { k_point_weights<<<ceil_div(B.n, 256), 256, 0, s>>>(B.d_perm, B.n, B.dim, B.d_X, nullptr, nullptr, B.kp,
                                                        B.d_sw, B.d_dg); ::h2mg::count_launch(); }
   H2_LAUNCH_CHECK();
+  if (own_bases) build_bases(B);
   build_blocks(B, &A);
   setup_operators(B);
   H2_CUDA(cudaStreamSynchronize(s));
@@ -346,6 +357,35 @@ h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int6
   });
 }
 
+h2mg_status h2mg_apply_ex(h2mg_matrix A, int precision, const double* x, double* y, int nrhs, int64_t ld,
+                          void* stream) {
+  return guard([&]() -> h2mg_status {
+    H2_REQUIRE(A && x && y, H2MG_ERR_INVALID_ARG, "null pointer argument");
+    Matrix& M = A->M;
+    H2_REQUIRE(nrhs >= 1 && ld >= M.n, H2MG_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= n");
+    H2_REQUIRE(precision == H2MG_PREC_F64 || precision == H2MG_PREC_MIXED_F32 || precision == H2MG_PREC_TF32X3,
+               H2MG_ERR_INVALID_ARG, "precision must be F64, MIXED_F32 or TF32X3");
+    H2_REQUIRE(precision == H2MG_PREC_F64 || M.with_f32, H2MG_ERR_INVALID_ARG,
+               "the FP32 and tensor-core products need a matrix built with_f32");
+    H2_REQUIRE(precision != H2MG_PREC_TF32X3 || panel_supported(M), H2MG_ERR_UNSUPPORTED,
+               "the tensor-core product needs leaf and rank blocks of 64");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == H2MG_PREC_TF32X3) {
+      ColsView X(x, M.n, ld, nrhs, true, false, s), Y(y, M.n, ld, nrhs, false, false, s);
+      apply_panel(M, X.d, X.ldd, Y.d, Y.ldd, nrhs, s);
+      Y.copy_out(y, s);
+      return H2MG_OK;
+    }
+    for (int c = 0; c < nrhs; c += NRMAX) {
+      const int g = std::min(NRMAX, nrhs - c);
+      ColsView X(x + (int64_t)c * ld, M.n, ld, g, true, false, s), Y(y + (int64_t)c * ld, M.n, ld, g, false, false, s);
+      apply_level_multi(M, 1, precision == H2MG_PREC_MIXED_F32, X.d, X.ldd, Y.d, Y.ldd, g, s);
+      Y.copy_out(y + (int64_t)c * ld, s);
+    }
+    return H2MG_OK;
+  });
+}
+
 h2mg_status h2mg_solve(h2mg_matrix A, const double* b, double* x, int nrhs, int64_t ld,
                        const h2mg_solve_opts* o, h2mg_solve_info* info, void* stream) {
   return guard([&]() -> h2mg_status {
@@ -465,6 +505,9 @@ h2mg_status h2mg_query(h2mg_matrix A, int what, int arg, int64_t* value) {
         v = op.bytes(4, 4);
         break;
       }
+      case H2MG_Q_PANEL_ENTRIES:
+        v = panel_entries(M);
+        break;
       default:
         throw Error{H2MG_ERR_INVALID_ARG, "unknown query"};
     }

@@ -62,6 +62,7 @@ struct Profile {
 };
 
 struct GraphSet;   // captured V-cycles of a matrix (solve.cu)
+struct PanelPlan;  // block lists and panels of the tensor-core product (panel.cu)
 
 // Host-side copy of a full (both triangles) CSR list of cluster pairs.
 struct HostCSR {
@@ -152,6 +153,7 @@ struct Matrix {
 
   Profile prof;
   GraphSet* graphs = nullptr;   // captured V-cycle graphs, by solve settings
+  PanelPlan* panel = nullptr;   // tensor-core product plan, built on first use
   cudaStream_t cap_stream = nullptr;
   std::vector<DevBuf> owned;    // everything else
   ~Matrix();
@@ -191,6 +193,13 @@ int64_t apply_bytes(const Matrix& M, int i);
 // split of the fastest timed trial. out (cap entries of 4 doubles) receives
 // (operator index, nr, fixed-heuristic ms, tuned ms) per tuned combination.
 int autotune_products(Matrix& M, cudaStream_t s, double* out, int cap);
+// ---- panel.cu
+// Y = A X at level 1 for nr columns on the tensor cores (split-TF32 products of the FP32
+// blocks, 128 columns per pass); synchronises s.
+void apply_panel(Matrix& M, const double* x, int64_t ldx, double* y, int64_t ldy, int nr, cudaStream_t s);
+bool panel_supported(const Matrix& M);
+int64_t panel_entries(const Matrix& M);   // block products of one pass (0: no plan yet)
+void destroy_panel_plan(Matrix& M);
 // ---- solve.cu
 void smooth(Matrix& M, int i, bool f32, const double* f, const double* x0, int n, double* x,
             double* r, cudaStream_t s);

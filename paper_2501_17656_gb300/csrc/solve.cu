@@ -805,11 +805,16 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
     outer_residual(M, o, b, x, r, W.t2, n, nr, s, near);
     dots_host(M, r, r, n, nr, rel, s);
     if (o.residual_dd == 2) {
-      // a column switches to the extended product once its float64 residual is within
-      // 100 tol, or has not reached a new minimum for 5 cycles (the float64 sum's
-      // rounding floor, which can lie near or above tol); this cycle is re-checked
-      bool redo = false;
+      // A column switches to the extended product once its float64 residual is within
+      // 100 tol. A column whose float64 residual has made no new minimum for 5 cycles
+      // is probed: its residual is recomputed with the extended product, and if that
+      // is below 0.8 of the float64 one, the float64 residual is dominated by the
+      // rounding of its sum (the floor, which can lie near or above tol) and the
+      // column switches; otherwise the stagnation is the iteration's own and float64
+      // stays. Either way this cycle uses the recomputed residual.
+      bool redo = false, probe[NRMAX];
       for (int c = 0; c < nr; ++c) {
+        probe[c] = false;
         const double rr = nb[c] > 0 ? std::sqrt(rel[c]) / nb[c] : 0.0;
         if (near[c] || done[c] || !std::isfinite(rr)) continue;
         if (rr < best[c]) {
@@ -818,11 +823,24 @@ h2mg_status solve_multi(Matrix& M, const double* b, double* x, int nr, const h2m
         } else {
           ++since[c];
         }
-        if (rr <= 100.0 * o.tol || since[c] >= 5) near[c] = redo = true;
+        if (rr <= 100.0 * o.tol)
+          near[c] = redo = true;
+        else if (since[c] >= 5)
+          probe[c] = redo = true;
       }
       if (redo) {
-        outer_residual(M, o, b, x, r, W.t2, n, nr, s, near);
-        dots_host(M, r, r, n, nr, rel, s);
+        bool ext[NRMAX];
+        for (int c = 0; c < nr; ++c) ext[c] = near[c] || probe[c];
+        double reld[NRMAX];
+        outer_residual(M, o, b, x, r, W.t2, n, nr, s, ext);
+        dots_host(M, r, r, n, nr, reld, s);
+        for (int c = 0; c < nr; ++c) {
+          if (probe[c]) {
+            if (std::sqrt(reld[c]) < 0.8 * std::sqrt(rel[c])) near[c] = true;
+            since[c] = 0;
+          }
+          rel[c] = reld[c];
+        }
       }
     }
     graph_collect(M);

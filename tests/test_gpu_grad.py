@@ -55,6 +55,31 @@ def test_derivative_sibling_matches_oracle(data):
     A.close()
 
 
+def test_skeleton_sibling_has_its_own_skeletons(data):
+    """A sibling of a skeleton matrix skeletonizes the derivative kernel itself on the
+    same tree: ranks and product equal to the oracle's derivative matrix, and within the
+    basis tolerance of the dense derivative kernel."""
+    X, _, _ = data
+    kw = dict(basis="skeleton", basis_tol=1e-9)
+    A = pkg.H2Matrix(torch.from_numpy(X).cuda(), "matern32", length=L_, nugget=S_, leaf=32, q=4, **kw)
+    dA = A.sibling("dmatern32_dl", length=L_)
+    h = H2Matrix(X, KernelSpec("matern32", L_, S_), 32, 4, 1.0, basis="skeleton", tol=1e-9)
+    dh = derivative_h2(h, KernelSpec("dmatern32_dl", L_, 0.0))
+    for ell in range(dh.tstar, dh.L + 1):
+        assert list(dA.export("RANKS", ell)) == [dh.rank[(ell, j)] for j in range(1 << ell)], ell
+    v = np.random.default_rng(5).standard_normal(N)
+    got = dA.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    ref = dh.apply(v)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    Xt = torch.from_numpy(X).cuda()
+    r = torch.cdist(Xt, Xt)
+    Kd = 3.0 * r ** 2 / L_ ** 3 * torch.exp(-math.sqrt(3.0) * r / L_)
+    exact = (Kd @ torch.from_numpy(v).cuda()).cpu().numpy()
+    assert np.linalg.norm(got - exact) / np.linalg.norm(exact) < 1e-10
+    dA.close()
+    A.close()
+
+
 def test_adjoint_gradients_match_oracle(data):
     X, y, b = data
     L, gy, gb, gl, gs = gpu_loss_grads(X, y, b, L_, S_)

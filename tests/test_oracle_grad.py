@@ -78,3 +78,26 @@ def test_gradients_match_dense_autograd():
     assert abs(ds - st.grad.item()) <= 1e-5 * abs(st.grad.item())
     assert np.linalg.norm(w - bt.grad.numpy()) <= 1e-6 * np.linalg.norm(w)
     assert np.linalg.norm(a - yt.grad.numpy()) <= 1e-6 * np.linalg.norm(a)
+
+
+def test_skeleton_derivative_matrix_has_its_own_skeletons():
+    """With skeleton bases, dA/dl is the derivative kernel's own skeleton H2 matrix on A's
+    tree and partition: within the basis tolerance of the dense derivative kernel
+    (3 r^2 / l^3) exp(-sqrt3 r / l) (zero diagonal), with skeletons of its own."""
+    rng = np.random.default_rng(8)
+    X = rng.random((3000, 3))
+    l = 0.1
+    A = H2Matrix(X, KernelSpec("matern32", l, 1e-2), 32, 4, 1.0, basis="skeleton", tol=1e-9)
+    assert A.tstar is not None
+    dA = derivative_h2(A, KernelSpec("dmatern32_dl", l, 0.0))
+    assert dA.tree is A.tree and dA.far is A.far
+    Kd = dense_kernel_matrix("dmatern32_dl", X, l, 0.0)
+    assert np.abs(np.diag(Kd)).max() == 0.0
+    v = rng.standard_normal(3000)
+    ref = Kd @ v
+    # its own skeletons: ~5e-13 here; the matrix's skeletons with derivative couplings
+    # would give ~1e-7 (they do not span the derivative kernel's far field)
+    assert np.linalg.norm(dA.apply(v) - ref) / np.linalg.norm(ref) < 1e-10
+    # the derivative kernel's skeletons differ from the matrix's own somewhere
+    diff = [key for key in A.skeletons.skel if not np.array_equal(A.skeletons.skel[key], dA.skeletons.skel[key])]
+    assert diff
