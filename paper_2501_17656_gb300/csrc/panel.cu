@@ -22,7 +22,9 @@
 // summed over a whole block row (hundreds of MMAs) it left errors near 1e-5. So each
 // entry's products go to fresh TMEM accumulators (the head products in one, the two
 // correction products in another, 8 and 16 MMAs), which the threads read after the
-// entry and add, rounding to nearest, into registers: FP32-level accuracy.
+// entry and add, rounding to nearest, into registers: FP32-level accuracy. Two sets of
+// accumulators alternate between entries, so that entry j - 1's are read while entry j's
+// MMAs run.
 //
 // The symmetric operators are stored as their upper triangle. Here they are read in full:
 // block (t, s), s > t, is staged for row t (read by rows) and again, transposed, for row s
@@ -42,7 +44,7 @@ constexpr uint32_t kTileA = PW * PK * 4;         // one A tile (hi or lo): 32 KB
 constexpr uint32_t kTileB = PK * PK * 4;         // one B tile: 16 KB
 constexpr uint32_t kStage = 2 * kTileA + 2 * kTileB;
 constexpr uint32_t kDynSmem = kStage + 1024;     // + alignment of the swizzle atoms
-constexpr uint32_t kTmemCols = 128;              // two FP32 accumulators of 64 columns x 128 lanes
+constexpr uint32_t kTmemCols = 256;              // 2 sets x 2 FP32 accumulators of 64 columns x 128 lanes
 // Instruction descriptor of tcgen05.mma kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
 // (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(PK >> 3) << 17) |
@@ -88,10 +90,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// Round an FP32 value to TF32 (10 fraction bits), to nearest with ties away from zero:
+// add half a unit of the 13 dropped bits to the magnitude's bit pattern (a carry moves
+// into the exponent correctly) and clear them. Two integer operations, where a
+// conversion instruction runs on the slower conversion pipe.
 __device__ __forceinline__ float tf32_rn(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void split4(const float4& v, float4& hi, float4& lo) {
@@ -148,25 +152,28 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
-// 8 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
 }
 
 // acc += the entry's head and correction accumulators (columns c0..c0+31 of this
-// thread's lane), added in that order with round-to-nearest.
+// thread's lane), their sum rounded to nearest.
 __device__ __forceinline__ void tmem_accumulate(uint32_t taddr, float* acc) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint32_t h[8], c[8];
-    tmem_ld8(taddr + 8 * q, h);
-    tmem_ld8(taddr + 64 + 8 * q, c);
+  for (int q = 0; q < 2; ++q) {
+    uint32_t h[16], c[16];
+    tmem_ld16(taddr + 16 * q, h);
+    tmem_ld16(taddr + 64 + 16 * q, c);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[8 * q + j] += __uint_as_float(h[j]) + __uint_as_float(c[j]);
+    for (int j = 0; j < 16; ++j) acc[16 * q + j] += __uint_as_float(h[j]) + __uint_as_float(c[j]);
   }
 }
 
@@ -205,6 +212,10 @@ __device__ __forceinline__ float4 transpose4(const float4& v, int lane) {
   return make_float4(o[0], o[1], o[2], o[3]);
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Global loads of one entry: the panel (W x 64 FP32, 8 float4 per thread) and the block
 // (4 float4 per thread, position by mode).
 __device__ __forceinline__ void load_entry(const PanelArgs& a, int e, int tid, float4* pa, float4* pb) {
@@ -227,38 +238,50 @@ __device__ __forceinline__ void store_entry(uint8_t* sm, int md, int tid, const 
   uint8_t* Bh = sm + 2 * kTileA;
   uint8_t* Bl = Bh + kTileB;
   float4 hi, lo;
+  // float4 q = tid + 256 i is row (tid >> 4) + 16 i, elements 4 (tid & 15) ..: the rows
+  // advance by two 8-row groups (2048 B) per i and the swizzle phase stays
+  const uint32_t offa = swz<PW>(tid >> 4, (tid & 15) << 2);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int q = tid + 256 * i;
-    const uint32_t off = swz<PW>(q >> 4, (q & 15) << 2);
     split4(pa[i], hi, lo);
-    *reinterpret_cast<float4*>(Ah + off) = hi;
-    *reinterpret_cast<float4*>(Al + off) = lo;
+    *reinterpret_cast<float4*>(Ah + offa + 2048 * i) = hi;
+    *reinterpret_cast<float4*>(Al + offa + 2048 * i) = lo;
   }
   const int lane = tid & 31;
+  if (md == BM_NAT) {
+    // natural column-major block whose column n is row n of the operand (same pattern)
+    const uint32_t offb = swz<PK>(tid >> 4, (tid & 15) << 2);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    uint32_t off;
-    float4 v = pb[i];
-    if (md == BM_NAT) {
-      // natural column-major block whose column n is row n of the operand
-      const int q = tid + 256 * i;
-      off = swz<PK>(q >> 4, (q & 15) << 2);
-    } else {
-      // swizzled block: float4 index q holds rows r0..r0+3 of column c
-      const int q = ((tid & ~31) | swz_lane_pos(lane)) + 256 * i;
-      const int l = q & 31, tk = q >> 5;
-      const int c = 4 * (tk >> 1) + (l >> 3), r0 = 8 * (l & 7) + 4 * (tk & 1);
-      if (md == BM_COL) {
-        off = swz<PK>(c, r0);                       // column c of the block is operand row c
-      } else {
-        v = transpose4(v, lane);                    // row r0 + cc, columns c - cc .. c - cc + 3
-        off = swz<PK>(r0 + (lane & 3), c - (lane & 3));
-      }
+    for (int i = 0; i < 4; ++i) {
+      split4(pb[i], hi, lo);
+      *reinterpret_cast<float4*>(Bh + offb + 2048 * i) = hi;
+      *reinterpret_cast<float4*>(Bl + offb + 2048 * i) = lo;
     }
-    split4(v, hi, lo);
-    *reinterpret_cast<float4*>(Bh + off) = hi;
-    *reinterpret_cast<float4*>(Bl + off) = lo;
+    return;
+  }
+  // swizzled block: float4 index q holds rows r0..r0+3 of column c; with
+  // q = (warp base | lane position) + 256 i the column advances by 16 per i
+  const int q0 = (tid & ~31) | swz_lane_pos(lane);
+  const int l = q0 & 31, tk = q0 >> 5;
+  const int c0 = 4 * (tk >> 1) + (l >> 3), r0 = 8 * (l & 7) + 4 * (tk & 1);
+  if (md == BM_COL) {
+    const uint32_t offb = swz<PK>(c0, r0);          // column c of the block is operand row c
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      split4(pb[i], hi, lo);
+      *reinterpret_cast<float4*>(Bh + offb + 2048 * i) = hi;
+      *reinterpret_cast<float4*>(Bl + offb + 2048 * i) = lo;
+    }
+  } else {
+    const int cc = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 v = transpose4(pb[i], lane);   // row r0 + cc, columns c - cc .. c - cc + 3
+      const uint32_t off = swz<PK>(r0 + cc, c0 + 16 * i - cc);
+      split4(v, hi, lo);
+      *reinterpret_cast<float4*>(Bh + off) = hi;
+      *reinterpret_cast<float4*>(Bl + off) = lo;
+    }
   }
 }
 
@@ -298,28 +321,30 @@ __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
   bool bad = false;
   for (int j = 0; j < ne; ++j) {
     if (j > 0) {
-      // the previous entry's products are complete: they have read the staging tiles,
-      // and their accumulators are added into v before the next entry overwrites them
+      // entry j - 1's products are complete: they have read the staging tiles
       int ok = 1;
       if (tid == 0) ok = mbar_wait(smem_u32(&bar), (uint32_t)((j - 1) & 1));
       if (__syncthreads_or(!ok)) {
         bad = true;
         break;
       }
-      tc_fence_after();
-      tmem_accumulate(tacc, v);
-      tc_fence_before();
     }
     store_entry(sm, a.mode[e0 + j], tid, pa, pb);
     fence_async_smem();
+    tc_fence_before();    // the reads of the set that entry j's products will overwrite
     __syncthreads();
     if (j + 1 < ne) load_entry(a, e0 + j + 1, tid, pa, pb);   // in flight during the products
+    if (tid == 32 && j + 2 < ne) {                            // and the entry after, into L2
+      prefetch_l2(a.blk[e0 + j + 2], PK * PK * 4);
+      prefetch_l2(a.xin + (size_t)a.col[e0 + j + 2] * PW * PK, PW * PK * 4);
+    }
     if (tid == 0) {
       tc_fence_after();
+      const uint32_t set = tmem + (uint32_t)(j & 1) * 128;
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
         const uint32_t ta = p == 2 ? sAl : sAh, tb = p == 1 ? sBl : sBh;
-        const uint32_t td = p == 0 ? tmem : tmem + 64;     // head / correction accumulator
+        const uint32_t td = p == 0 ? set : set + 64;       // head / correction accumulator
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
           const uint64_t da = sw128_desc(ta + (s >> 2) * (PW * 128) + (s & 3) * 32);
@@ -328,6 +353,11 @@ __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
         }
       }
       mma_commit(smem_u32(&bar));
+    }
+    if (j > 0) {
+      // entry j - 1's accumulators, while entry j's products run
+      tc_fence_after();
+      tmem_accumulate(tacc + (uint32_t)((j - 1) & 1) * 128, v);
     }
     issued = j + 1;
   }
@@ -338,7 +368,7 @@ __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
       bad = true;
     } else {
       tc_fence_after();
-      tmem_accumulate(tacc, v);
+      tmem_accumulate(tacc + (uint32_t)((issued - 1) & 1) * 128, v);
     }
   } else if (issued > 0) {
     // a wait ran out: give the products in flight one more bounded wait before the
