@@ -10,9 +10,12 @@
 //
 // with one CTA per output row, D in tensor memory (TMEM, 128 lanes = the W columns of
 // the panel, 64 FP32 columns), and W = 128 so that every tcgen05.mma is the full
-// 128 x 64 x 8 shape. Operands are staged in shared memory by the CTA's threads (the
-// blocks are read through registers, where they are also rearranged and split), in the
-// 128-byte-swizzled K-major layout of tcgen05 shared-memory descriptors.
+// 128 x 64 x 8 shape. Operands sit in shared memory in the 128-byte-swizzled K-major
+// layout of tcgen05 shared-memory descriptors. Panels that later steps read as operands
+// are written once, by their producer, already split into their TF32 head and tail tiles
+// in that layout (64 KB per panel), so that one thread moves an entry's panel into shared
+// memory with bulk copies (cp.async.bulk, completion on an mbarrier); the blocks are read
+// through registers, where the CTA's threads rearrange and split them.
 //
 // Precision: the blocks are the FP32 copy. Each FP32 operand a is split into
 // a_hi = tf32(a) (rounded to nearest) and a_lo = tf32(a - a_hi), and every block product
@@ -43,6 +46,7 @@ constexpr int PK = 64;                           // block edge (MMA N and contra
 constexpr uint32_t kTileA = PW * PK * 4;         // one A tile (hi or lo): 32 KB
 constexpr uint32_t kTileB = PK * PK * 4;         // one B tile: 16 KB
 constexpr uint32_t kStage = 2 * kTileA + 2 * kTileB;
+constexpr uint32_t kPanelSP = 2 * kTileA;        // a split panel: head tile, then tail tile
 constexpr uint32_t kDynSmem = kStage + 1024;     // + alignment of the swizzle atoms
 constexpr uint32_t kTmemCols = 256;              // 2 sets x 2 FP32 accumulators of 64 columns x 128 lanes
 // Instruction descriptor of tcgen05.mma kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
@@ -58,9 +62,10 @@ struct PanelArgs {
   const int* col;                    // [nnz] input panel of the entry
   const float* const* blk;           // [nnz] 64 x 64 FP32 block of the entry
   const unsigned char* mode;         // [nnz] BM_*: how the block is read
-  const float* xin;                  // input panels
-  const float* cin;                  // addend panels (row + cin_off) or null
-  float* out;                        // output panels (row + out_off) or null: scatter
+  const char* xin;                   // input panels, split (kPanelSP bytes each)
+  const float* cin;                  // addend panels, plain FP32 [W][64] (row + cin_off), or null
+  void* out;                         // output panels (row + out_off), or null: scatter
+  int out_split;                     // 1: outputs split like the inputs, 0: plain FP32
   int64_t cin_off, out_off;
   const int* leafoff;                // scatter: leaf offsets in tree order
   const int* perm;                   //          tree position -> user index
@@ -112,6 +117,18 @@ __device__ __forceinline__ void split4(const float4& v, float4& hi, float4& lo) 
 __device__ __forceinline__ void mbar_init(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Global -> shared bulk copy (16-byte aligned, a multiple of 16 bytes) whose completion
+// counts `bytes` on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
@@ -216,40 +233,33 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Global loads of one entry: the panel (W x 64 FP32, 8 float4 per thread) and the block
-// (4 float4 per thread, position by mode).
-__device__ __forceinline__ void load_entry(const PanelArgs& a, int e, int tid, float4* pa, float4* pb) {
-  const float4* X = reinterpret_cast<const float4*>(a.xin + (size_t)a.col[e] * PW * PK);
+// Global loads of one entry's block (4 float4 per thread, position by mode).
+__device__ __forceinline__ void load_block(const PanelArgs& a, int e, int tid, float4* pb) {
   const float4* B = reinterpret_cast<const float4*>(a.blk[e]);
-  const int md = a.mode[e];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) pa[i] = __ldg(X + tid + 256 * i);
-  const int q0 = md == BM_NAT ? tid : ((tid & ~31) | swz_lane_pos(tid & 31));
+  const int q0 = a.mode[e] == BM_NAT ? tid : ((tid & ~31) | swz_lane_pos(tid & 31));
 #pragma unroll
   for (int i = 0; i < 4; ++i) pb[i] = __ldg(B + q0 + 256 * i);
 }
 
-// Shared-memory stores of one entry: A = panel^T (row w = right-hand side), B = the block
-// as "n-rows" (row n holds the 64 contraction elements of output column n), each as its
-// TF32 head and tail tiles.
-__device__ __forceinline__ void store_entry(uint8_t* sm, int md, int tid, const float4* pa, const float4* pb) {
-  uint8_t* Ah = sm;
-  uint8_t* Al = sm + kTileA;
+// One thread: the entry's split panel (head and tail tiles, 64 KB) into the A tiles.
+__device__ __forceinline__ void copy_panel(const PanelArgs& a, int e, uint32_t sA, uint32_t bar) {
+  const char* src = a.xin + (size_t)a.col[e] * kPanelSP;
+  mbar_expect_tx(bar, kPanelSP);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) bulk_g2s(sA + c * (kPanelSP / 4), src + c * (kPanelSP / 4), kPanelSP / 4, bar);
+}
+
+// Shared-memory stores of one entry's block as the B operand in "n-rows" form (row n
+// holds the 64 contraction elements of output column n), as TF32 head and tail tiles.
+__device__ __forceinline__ void store_block(uint8_t* sm, int md, int tid, const float4* pb) {
   uint8_t* Bh = sm + 2 * kTileA;
   uint8_t* Bl = Bh + kTileB;
   float4 hi, lo;
-  // float4 q = tid + 256 i is row (tid >> 4) + 16 i, elements 4 (tid & 15) ..: the rows
-  // advance by two 8-row groups (2048 B) per i and the swizzle phase stays
-  const uint32_t offa = swz<PW>(tid >> 4, (tid & 15) << 2);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    split4(pa[i], hi, lo);
-    *reinterpret_cast<float4*>(Ah + offa + 2048 * i) = hi;
-    *reinterpret_cast<float4*>(Al + offa + 2048 * i) = lo;
-  }
   const int lane = tid & 31;
   if (md == BM_NAT) {
-    // natural column-major block whose column n is row n of the operand (same pattern)
+    // natural column-major block whose column n is row n of the operand: float4
+    // q = tid + 256 i is row (tid >> 4) + 16 i, elements 4 (tid & 15) .., so the rows
+    // advance by two 8-row groups (2048 B) per i and the swizzle phase stays
     const uint32_t offb = swz<PK>(tid >> 4, (tid & 15) << 2);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -287,7 +297,8 @@ __device__ __forceinline__ void store_entry(uint8_t* sm, int md, int tid, const 
 
 __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
   extern __shared__ uint8_t dsm[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar;      // the entry's MMAs have completed
+  __shared__ uint64_t bar_a;    // the entry's panel has arrived
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = blockIdx.x;
@@ -302,7 +313,10 @@ __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) mbar_init(smem_u32(&bar));
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar));
+    mbar_init(smem_u32(&bar_a));
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -315,41 +329,55 @@ __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
   float v[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = 0.f;
-  float4 pa[8], pb[4];
-  if (ne > 0) load_entry(a, e0, tid, pa, pb);
-  int issued = 0;
+  float4 pb[4];
+  int issued = 0;         // entries whose MMAs were committed
+  int copied = 0;         // thread 0: panels whose copy was started
+  int t0ok = 1;           // thread 0: every wait so far completed
   bool bad = false;
+  if (ne > 0) {
+    load_block(a, e0, tid, pb);
+    if (tid == 0) {
+      copy_panel(a, e0, sAh, smem_u32(&bar_a));
+      copied = 1;
+    }
+  }
   for (int j = 0; j < ne; ++j) {
     if (j > 0) {
       // entry j - 1's products are complete: they have read the staging tiles
-      int ok = 1;
-      if (tid == 0) ok = mbar_wait(smem_u32(&bar), (uint32_t)((j - 1) & 1));
-      if (__syncthreads_or(!ok)) {
+      if (tid == 0) t0ok &= mbar_wait(smem_u32(&bar), (uint32_t)((j - 1) & 1));
+      if (__syncthreads_or(tid == 0 && !t0ok)) {
         bad = true;
         break;
       }
+      if (tid == 0) {
+        copy_panel(a, e0 + j, sAh, smem_u32(&bar_a));
+        copied = j + 1;
+      }
     }
-    store_entry(sm, a.mode[e0 + j], tid, pa, pb);
+    store_block(sm, a.mode[e0 + j], tid, pb);
     fence_async_smem();
     tc_fence_before();    // the reads of the set that entry j's products will overwrite
     __syncthreads();
-    if (j + 1 < ne) load_entry(a, e0 + j + 1, tid, pa, pb);   // in flight during the products
+    if (j + 1 < ne) load_block(a, e0 + j + 1, tid, pb);      // in flight during the products
     if (tid == 32 && j + 2 < ne) {                            // and the entry after, into L2
       prefetch_l2(a.blk[e0 + j + 2], PK * PK * 4);
-      prefetch_l2(a.xin + (size_t)a.col[e0 + j + 2] * PW * PK, PW * PK * 4);
+      prefetch_l2(a.xin + (size_t)a.col[e0 + j + 2] * kPanelSP, kPanelSP);
     }
     if (tid == 0) {
+      t0ok &= mbar_wait(smem_u32(&bar_a), (uint32_t)(j & 1));   // the panel is in place
       tc_fence_after();
       const uint32_t set = tmem + (uint32_t)(j & 1) * 128;
+      if (t0ok) {
 #pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        const uint32_t ta = p == 2 ? sAl : sAh, tb = p == 1 ? sBl : sBh;
-        const uint32_t td = p == 0 ? set : set + 64;       // head / correction accumulator
+        for (int p = 0; p < 3; ++p) {
+          const uint32_t ta = p == 2 ? sAl : sAh, tb = p == 1 ? sBl : sBh;
+          const uint32_t td = p == 0 ? set : set + 64;     // head / correction accumulator
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const uint64_t da = sw128_desc(ta + (s >> 2) * (PW * 128) + (s & 3) * 32);
-          const uint64_t db = sw128_desc(tb + (s >> 2) * (PK * 128) + (s & 3) * 32);
-          mma_tf32(td, da, db, (p == 2 || s > 0) ? 1u : 0u);
+          for (int s = 0; s < 8; ++s) {
+            const uint64_t da = sw128_desc(ta + (s >> 2) * (PW * 128) + (s & 3) * 32);
+            const uint64_t db = sw128_desc(tb + (s >> 2) * (PK * 128) + (s & 3) * 32);
+            mma_tf32(td, da, db, (p == 2 || s > 0) ? 1u : 0u);
+          }
         }
       }
       mma_commit(smem_u32(&bar));
@@ -362,20 +390,21 @@ __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
     issued = j + 1;
   }
   if (issued > 0 && !bad) {
-    int ok = 1;
-    if (tid == 0) ok = mbar_wait(smem_u32(&bar), (uint32_t)((issued - 1) & 1));
-    if (__syncthreads_or(!ok)) {
+    if (tid == 0) t0ok &= mbar_wait(smem_u32(&bar), (uint32_t)((issued - 1) & 1));
+    if (__syncthreads_or(tid == 0 && !t0ok)) {
       bad = true;
     } else {
       tc_fence_after();
       tmem_accumulate(tacc + (uint32_t)((issued - 1) & 1) * 128, v);
     }
-  } else if (issued > 0) {
-    // a wait ran out: give the products in flight one more bounded wait before the
-    // accumulators are released
-    if (tid == 0) mbar_wait(smem_u32(&bar), (uint32_t)((issued - 1) & 1));
-    __syncthreads();
   }
+  if (bad && tid == 0) {
+    // a wait ran out: one more bounded wait for the copies and products in flight before
+    // the shared memory and the accumulators are released
+    if (copied > 0) mbar_wait(smem_u32(&bar_a), (uint32_t)((copied - 1) & 1));
+    if (issued > 0) mbar_wait(smem_u32(&bar), (uint32_t)((issued - 1) & 1));
+  }
+  __syncthreads();
   if (bad) {
     if (tid == 0) atomicExch(a.flag, 1);
   } else {
@@ -390,8 +419,20 @@ __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
         v[4 * j + 3] += c.w;
       }
     }
-    if (a.out) {
-      float4* O = reinterpret_cast<float4*>(a.out + ((size_t)(row + a.out_off) * PW + w) * PK + 32 * h);
+    if (a.out && a.out_split) {
+      // split panel: elements 32 h + 4 j .. of row w in the head and tail tiles
+      char* O = reinterpret_cast<char*>(a.out) + (size_t)(row + a.out_off) * kPanelSP;
+      float4 hi, lo;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        split4(make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]), hi, lo);
+        const uint32_t off = swz<PW>(w, 32 * h + 4 * j);
+        *reinterpret_cast<float4*>(O + off) = hi;
+        *reinterpret_cast<float4*>(O + kTileA + off) = lo;
+      }
+    } else if (a.out) {
+      float4* O = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out) +
+                                            ((size_t)(row + a.out_off) * PW + w) * PK + 32 * h);
 #pragma unroll
       for (int j = 0; j < 8; ++j) O[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     } else {
@@ -416,10 +457,10 @@ __global__ void __launch_bounds__(256, 2) k_panel_mma(PanelArgs a) {
   }
 }
 
-// Float64 columns (user order, leading dimension ldx) -> point panels [leaf][W][64], zero
-// in padded slots and unused columns.
+// Float64 columns (user order, leading dimension ldx) -> split point panels (one per
+// leaf), zero in padded slots and unused columns.
 __global__ void k_panel_in(const double* __restrict__ x, int64_t ldx, int nr, const int* __restrict__ leafoff,
-                           const int* __restrict__ perm, int nleaf, float* __restrict__ xp) {
+                           const int* __restrict__ perm, int nleaf, char* __restrict__ xp) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t l = idx / (PW * PK);
   if (l >= nleaf) return;
@@ -427,7 +468,10 @@ __global__ void k_panel_in(const double* __restrict__ x, int64_t ldx, int nr, co
   const int p0 = leafoff[l], nl = leafoff[l + 1] - p0;
   float v = 0.f;
   if (w < nr && i < nl) v = (float)x[(int64_t)perm[p0 + i] + (int64_t)w * ldx];
-  xp[idx] = v;
+  const float hi = tf32_rn(v);
+  char* P = xp + (size_t)l * kPanelSP + swz<PW>(w, i);
+  *reinterpret_cast<float*>(P) = hi;
+  *reinterpret_cast<float*>(P + kTileA) = tf32_rn(v - hi);
 }
 
 }  // namespace
@@ -445,7 +489,8 @@ struct PanelCSR {
 struct PanelPlan {
   PanelCSR lup, near, coup, lfin;
   std::vector<PanelCSR> up, down;   // index: tree level ell
-  float *xp = nullptr, *xc = nullptr, *yr = nullptr, *yc = nullptr, *yp = nullptr;
+  char *xp = nullptr, *xc = nullptr, *yc = nullptr;   // split panels (operands of later steps)
+  float *yr = nullptr, *yp = nullptr;                 // plain panels (addends)
 };
 
 void destroy_panel_plan(Matrix& M) {
@@ -533,15 +578,15 @@ void build_plan(Matrix& M) {
   auto* P = new PanelPlan();
   M.panel = P;
   const size_t panel = (size_t)PW * PK;
-  P->xp = (float*)M.alloc(sizeof(float) * panel * nleaf);
+  P->xp = (char*)M.alloc((size_t)kPanelSP * nleaf);
   P->yp = (float*)M.alloc(sizeof(float) * panel * nleaf);
   P->near = full_list(M, M.opD);
   HostList fin;
   if (ts >= 0) {
     const size_t ns = (size_t)M.nslots();
-    P->xc = (float*)M.alloc(sizeof(float) * panel * ns);
+    P->xc = (char*)M.alloc((size_t)kPanelSP * ns);
     P->yr = (float*)M.alloc(sizeof(float) * panel * ns);
-    P->yc = (float*)M.alloc(sizeof(float) * panel * ns);
+    P->yc = (char*)M.alloc((size_t)kPanelSP * ns);
     P->coup = full_list(M, M.opC[1]);
     const size_t kk = (size_t)PK * PK;
     HostList lu;   // x_hat_l = U_l^T x_l: column b of U_l (column-major) is operand row b
@@ -576,8 +621,8 @@ void build_plan(Matrix& M) {
   P->lfin = upload_list(M, fin);
 }
 
-void launch(Matrix& M, const PanelCSR& C, const float* xin, const float* cin, int64_t cin_off, float* out,
-            int64_t out_off, double* y, int64_t ldy, int nr, cudaStream_t s) {
+void launch(Matrix& M, const PanelCSR& C, const char* xin, const float* cin, int64_t cin_off, void* out,
+            bool out_split, int64_t out_off, double* y, int64_t ldy, int nr, cudaStream_t s) {
   if (C.nrows == 0) return;
   PanelArgs a{};
   a.rowptr = C.rowptr;
@@ -587,6 +632,7 @@ void launch(Matrix& M, const PanelCSR& C, const float* xin, const float* cin, in
   a.xin = xin;
   a.cin = cin;
   a.out = out;
+  a.out_split = out_split ? 1 : 0;
   a.cin_off = cin_off;
   a.out_off = out_off;
   a.leafoff = M.d_leafoff;
@@ -628,16 +674,17 @@ void apply_panel(Matrix& M, const double* x, int64_t ldx, double* y, int64_t ldy
                                                                nleaf, P.xp); ::h2mg::count_launch(); }
     H2_LAUNCH_CHECK();
     if (ts >= 0) {
-      launch(M, P.lup, P.xp, nullptr, 0, P.xc, M.slot0(L), nullptr, 0, 0, s);
-      for (int ell = L; ell > ts; --ell) launch(M, P.up[ell], P.xc, nullptr, 0, P.xc, M.slot0(ell - 1), nullptr, 0, 0, s);
+      launch(M, P.lup, P.xp, nullptr, 0, P.xc, true, M.slot0(L), nullptr, 0, 0, s);
+      for (int ell = L; ell > ts; --ell)
+        launch(M, P.up[ell], P.xc, nullptr, 0, P.xc, true, M.slot0(ell - 1), nullptr, 0, 0, s);
     }
-    launch(M, P.near, P.xp, nullptr, 0, P.yp, 0, nullptr, 0, 0, s);
+    launch(M, P.near, P.xp, nullptr, 0, P.yp, false, 0, nullptr, 0, 0, s);
     if (ts >= 0) {
-      launch(M, P.coup, P.xc, nullptr, 0, P.yr, 0, nullptr, 0, 0, s);
+      launch(M, P.coup, P.xc, nullptr, 0, P.yr, false, 0, nullptr, 0, 0, s);
       for (int ell = ts; ell <= L; ++ell)
-        launch(M, P.down[ell], P.yc, P.yr, M.slot0(ell), P.yc, M.slot0(ell), nullptr, 0, 0, s);
+        launch(M, P.down[ell], P.yc, P.yr, M.slot0(ell), P.yc, true, M.slot0(ell), nullptr, 0, 0, s);
     }
-    launch(M, P.lfin, ts >= 0 ? P.yc : P.xp, P.yp, 0, nullptr, 0, y + (int64_t)c0 * ldy, ldy, g, s);
+    launch(M, P.lfin, ts >= 0 ? P.yc : P.xp, P.yp, 0, nullptr, false, 0, y + (int64_t)c0 * ldy, ldy, g, s);
   }
   int h = 0;
   H2_CUDA(cudaMemcpyAsync(&h, M.d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
