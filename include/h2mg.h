@@ -200,7 +200,7 @@ h2mg_status h2mg_apply(h2mg_matrix A, const double* x, double* y, int nrhs, int6
  *                        downward -- is a 64 x 64 block times a 64 x 128 panel. Each FP32
  *                        operand a is split into a TF32 head h = tf32(a) and tail
  *                        t = tf32(a - h), and a b is formed as h_a h_b + h_a t_b + t_a h_b
- *                        in FP32 (relative error of each product below about 2^-21).
+ *                        in FP32 (relative error of each product below 2^-20).
  *                        Needs leaf and rank blocks of 64 (KD = KC = 64). Each
  *                        off-diagonal stored block is read twice (once per triangle), so
  *                        that no output needs atomic sums. Synchronises the stream.

@@ -6,7 +6,7 @@ panels through tcgen05 with split-TF32 operands. Checks, column by column:
 
 * against the oracle's product on sampled columns, and against the float64 product on
   every column, with an error of the order of the FP32 copy's own (the split loses less
-  than 2^-21 per product);
+  than 2^-20 per product; tests/test_split_tf32.py);
 * panels of 1, 16, 64, 128 and 130 columns (a ragged second pass), host and device
   buffers, zero columns, and a matrix without far field (the leaf step has no entries);
 * the skeleton bases of the 2^20-point Gaussian's density;
