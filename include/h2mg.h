@@ -394,8 +394,7 @@ h2mg_status h2mg_autotune(h2mg_matrix A, void* stream, double* report, int cap, 
  * of 8 * clusters * KC bytes and two point buffers of 8 * leaves * KD bytes: about 64
  * bytes per point in 3-D with leaf 64 and 64 nodes, so some 2^18 such points fit).
  * Vectors must be n float64 entries on the current device. The first call on a device
- * looks up the array's address with
- * that device current; make that first call before any stream capture. All calls
+ * looks up the array's address with that device current. All calls
  * share the array and it keeps the last call's contents: calls whose work overlaps
  * on the GPU (different streams, or different host threads) race and give wrong
  * results. */
