@@ -199,12 +199,16 @@ __device__ __forceinline__ float pick(const float4& v, int i) {
 }
 
 // Float4 of the swizzled 64 x 64 FP32 block layout (one float4 = rows r0..r0+3 of one
-// column c) that thread lane `lane` of a warp loads for the row / column reads: a
-// permutation inside the warp's 512-byte segment, chosen so that the four lanes holding
-// the same four rows are neighbours (lane & ~3) and every group of 8 lanes stores to
-// at most two rows per bank after the 4 x 4 transposition below.
+// column c; position (cc << 3) | g holds column c0 + cc and rows 8 g + ..) that thread
+// lane `lane` of a warp loads for the row / column reads: a permutation inside the warp's
+// 512-byte segment. The four lanes holding the same rows are neighbours (lane & ~3, the
+// 4 x 4 transposition below). Each group of 8 lanes (one 16-byte store wavefront) takes
+// the row groups g and g + 2 (g in 0, 1, 4, 5): their 16-byte chunks differ in the third
+// bit of the swizzle phase, so the column reads store without bank conflicts (the row
+// reads with two lanes per bank).
 __device__ __forceinline__ int swz_lane_pos(int lane) {
-  const int cc = lane & 3, g = 2 * (lane >> 3) + ((lane >> 2) & 1);
+  const int cc = lane & 3, m = lane >> 3, b = (lane >> 2) & 1;
+  const int g = (m & 1) + 4 * (m >> 1) + 2 * b;
   return (cc << 3) | g;
 }
 
